@@ -1,0 +1,323 @@
+"""Throughput of the low-rank collided-proton transport solve on GB300.
+
+One bench step is one whole transport solve of the workload: the CSDA ray trace
+of the beam, every energy step of the low-rank integrator (streaming BUG with RK4,
+implicit collided scattering, first-collision source, truncations) and the dose.
+Default workload: 64^3 voxels of 2 mm water, one 150 MeV pencil beam, Boltzmann
+screened-Rutherford scattering (eta = 1e-3, extended transport correction),
+P_15 (256 moments), fixed rank 20, 200 energy steps 150 -> 1 MeV, FP32 n-side
+arithmetic with FP64 reductions/factorisations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores, each step a bounded
+sample (a few energy steps) of the same workload. Under torchrun each rank runs
+its own copy of the workload (beams are independent: weak scaling); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy steps/s and cell·rank updates/s per GB300, % HBM roofline, vs plain"
+UNIT = "energy steps/s"
+WORKLOAD = "water_64cube_boltzmann"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _workload():
+    from paper_2508_04484_gb300 import workloads as WL
+    return WL.water_64cube_boltzmann()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _rank_stats(log, nsub, n):
+    """Cell-rank updates and streaming-stage work of one solve from its rank log."""
+    K = len(nsub)
+    r_start = np.zeros(K, dtype=np.int64)
+    for k in range(1, K):
+        a, b = log[k - 1]
+        r_start[k] = b if b >= 0 else max(a, 0)
+    updates = int(np.sum(r_start) * n)
+    active = r_start > 0
+    stage_launches = int(np.sum(4 * np.asarray(nsub)[active]))
+    return r_start, updates, stage_launches
+
+
+def cpu_baseline(cfg, mats, w, beams, budget_steps=4):
+    """The FP64 oracle as it stands, on the host cores, for the first energy steps of
+    the workload (source from a single central ray of the beam)."""
+    from oracle import dlra as ODL
+    from oracle import problem as OP
+    from oracle import raytrace as ORT
+    prob = OP.Problem(cfg, mats, w)
+    b = dict(beams[0], spot_sigma=0.0)
+    r = ORT.trace(prob, b)
+    src = [(r.psi, r.e_u, np.asarray(b["dir"]))]
+    st = ODL.State(prob.n, prob.m)
+    rc = ODL.RankControl(mode=cfg["rank_mode"], rank=cfg["rank"], tol=cfg["trunc_tol"], r_max=cfg["rank_max"])
+    t0 = time.perf_counter()
+    upd = 0
+    for k in range(budget_steps):
+        upd += prob.n * st.r
+        ODL.step(prob, st, k, src, rc)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": budget_steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cell_rank_updates_per_s": upd / dt,
+            "sample": f"first {budget_steps} energy steps of {WORKLOAD} (source of one central ray), "
+                      f"{dt:.1f} s, numpy/BLAS threads on {cores} cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    cfg, mats, w, beams = _workload()
+    samples = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(cfg, mats, w, beams, budget_steps=2)
+        if i >= args.warmup:
+            samples.append(cb)
+    val = float(np.mean([s["value"] for s in samples]))
+    ms = 1000.0 / val * cfg["n_steps"]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "voxels": "64x64x64", "voxel_mm": 2.0, "sh_degree": 15,
+                       "rank": 20, "energy_steps": 200, "beams": 1,
+                       "reference_sample": "each step: 2 energy steps of the FP64 oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": samples[0]["cores"],
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2508_04484_gb300 import build as B
+    from paper_2508_04484_gb300 import dlra as D
+    B.build()
+    cfg, mats, w, beams = _workload()
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    K = cfg["n_steps"]
+    stream = torch.cuda.Stream(device=dev)
+    solver = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
+    nsub = solver.substeps()
+    dose = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def one_solve():
+        solver.reset(retrace=True)
+        solver.step(K)
+        solver.dose(out=dose)
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    log = solver.rank_log()
+    r_start, updates, stage_launches = _rank_stats(log, nsub, n)
+    clocks = Clocks(dev.index)
+    # ---- timed region: K whole solves, L2 flushed between them ----
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    solver.set_profiling(True)
+    launches0 = solver.launch_count()
+    times = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_solve()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    stage_ms, stage_count = solver.kernel_stats()
+    solver.set_profiling(False)
+    launches = solver.launch_count() - launches0
+    ms_per_solve = float(np.sum(times) / args.steps)
+    if ws > 1:
+        t = torch.tensor([ms_per_solve], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_solve = float(t.item())
+    value = ws * K / (ms_per_solve / 1000.0)
+    updates_per_s = ws * updates / (ms_per_solve / 1000.0)
+    # ---- roofline of the dominant kernel: fused streaming stage (stencil x r-by-r mix) ----
+    nk = 4 if cfg["ny"] == 1 and cfg["dy"] == 0 else 6
+    esize = 4 if cfg["precision"] == 1 else 8
+    act = r_start > 0
+    per_solve_launches = int(np.sum(4 * np.asarray(nsub)[act]))
+    bytes_solve = float(np.sum((4 * np.asarray(nsub) * n * (3 * r_start + 1) * esize)[act]))
+    flops_solve = float(np.sum((4 * np.asarray(nsub) * n * 2 * nk * r_start.astype(np.float64) ** 2)[act]))
+    avg_launch_ms = stage_ms / max(stage_count, 1)
+    avg_bytes = bytes_solve / max(per_solve_launches, 1)
+    avg_flops = flops_solve / max(per_solve_launches, 1)
+    peaks, src = _peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # FFMA, TFLOP/s
+    gbs = avg_bytes / (avg_launch_ms / 1000.0) / 1e9
+    tfs = avg_flops / (avg_launch_ms / 1000.0) / 1e12
+    frac_hbm = gbs / hbm_peak
+    frac_alu = tfs / fp32_peak
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
+                "traffic": None, "kernel": "gemm_kernel<ALoadStencil> (fused RK4 streaming stage)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
+                "achieved_gbs": gbs, "hbm_frac": frac_hbm, "avg_launch_us": avg_launch_ms * 1000.0}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                "traffic": None, "kernel": "gemm_kernel<ALoadStencil> (fused RK4 streaming stage)",
+                "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "alu_frac": frac_alu,
+                "avg_launch_us": avg_launch_ms * 1000.0}
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if rank == 0 or ws > 1:
+        w_host = np.ascontiguousarray(w, dtype=np.float64)
+        dose_host = np.zeros(n)
+        e2e_times = []
+        for i in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = D.Solver(cfg, mats, w_host, beams, stream=stream.cuda_stream)
+            s2.step(K)
+            s2.dose(out=dose_host)
+            e2e_times.append(time.perf_counter() - t0)
+            s2.close()
+        e2e_s = min(e2e_times)
+        e2e = {"value": ws * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w_host.nbytes),
+               "d2h_bytes_per_step": int(dose_host.nbytes),
+               "includes": "context creation with angular tables, host->device mixture weights, ray trace, "
+                           "all energy steps, dose read back to host"}
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cfg_c, mats_c, w_c, beams_c = _workload()
+        cb = cpu_baseline(cfg_c, mats_c, w_c, beams_c)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if cfg["precision"] == 1 else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "voxels": "64x64x64", "voxel_mm": 2.0, "material": "water",
+                           "beam_MeV": 150, "collision": "boltzmann screened-Rutherford eta=1e-3 + ETC",
+                           "sh_degree": 15, "moments": 256, "rank": 20, "energy_steps": K,
+                           "step": "one whole solve (ray trace + all energy steps + dose)",
+                           "l2": "flushed (256 MB write) between timed solves"},
+                "cell_rank_updates_per_s": updates_per_s,
+                "energy_steps_per_s": value,
+                "gpu_launches": int(launches),
+                "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
+                "vs_plain": None}
+        print(json.dumps(line))
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

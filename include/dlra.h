@@ -1,0 +1,194 @@
+/*
+ * dlra.h -- C ABI of the GB300 low-rank collided-proton transport library.
+ *
+ * The library advances the collided proton flux of arXiv 2508.04484 in energy
+ * (pseudo-time t = E_max - E, Sec. 3.3) as a rank-r factorisation
+ * u = X S W^T (Sec. 2.2) of its real spherical-harmonic moments (Sec. 3.3.1) on a
+ * uniform voxel grid (Sec. 3.3.2). One energy step is the Lie split of Sec. 3.3.3:
+ * streaming by the augmented BUG integrator with RK4 time updates, collided
+ * self-scattering by an implicit-Euler L-step, and the first-collision source of
+ * a CSDA ray tracer (Sec. 3.2) by augmented BUG K/L/S steps with explicit Euler.
+ *
+ * Units: cm, MeV, g/cm^3. Doses are per unit beam weight (one source proton for
+ * weight 1); 2-D slabs (ny == 1, dy == 0) are per unit length in y.
+ *
+ * Conventions for every entry point:
+ *  - All functions return a dlra_status; no exception crosses the ABI.
+ *  - Host pointers are read or written during the call only; the caller keeps
+ *    ownership. "on_device" arguments say a pointer is device memory of the
+ *    context's GPU; device pointers must be ordered with the context's stream.
+ *  - Matrices are dense; "column-major" means element (i, j) of an R x C matrix
+ *    is at [j * R + i].
+ *  - After DLRA_ERR_CUDA, DLRA_ERR_NONFINITE or DLRA_ERR_TIMEOUT the context is
+ *    poisoned: every later call returns the same status until dlra_destroy.
+ *  - A context is used by one host thread at a time; contexts are independent.
+ *  - dlra_last_error gives a one-line description of the last failure.
+ */
+#ifndef DLRA_H
+#define DLRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dlra_ctx dlra_ctx;
+
+typedef enum {
+  DLRA_OK = 0,
+  DLRA_ERR_ARG = 1,       /* invalid argument (size, pointer, value)          */
+  DLRA_ERR_STATE = 2,     /* call out of order (e.g. dlra_step before a beam) */
+  DLRA_ERR_CUDA = 3,      /* a CUDA runtime call or kernel failed             */
+  DLRA_ERR_OOM = 4,       /* device allocation failed                         */
+  DLRA_ERR_NONFINITE = 5, /* the low-rank state became non-finite             */
+  DLRA_ERR_RANK = 6,      /* rank bookkeeping failed (capacity exceeded)      */
+  DLRA_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up               */
+} dlra_status;
+
+enum { DLRA_FOKKER_PLANCK = 0, DLRA_BOLTZMANN = 1 };
+enum { DLRA_RANK_FIXED = 0, DLRA_RANK_ADAPTIVE = 1, DLRA_RANK_SCHEDULE = 2 };
+enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1 };
+
+/* Problem configuration (Sec. 3.3, Sec. 4).
+ *  nx, ny, nz, dx, dy, dz : voxel grid, cell index (k*ny + j)*nx + i (Sec. 3.3.2).
+ *                           ny == 1 && dy == 0 selects a 2-D x-z slab (no y streaming).
+ *  sh_degree              : N, m = (N+1)^2 moments (Sec. 3.3.1); 1 <= N <= 31.
+ *  collision              : DLRA_FOKKER_PLANCK or DLRA_BOLTZMANN (Sec. 2.1).
+ *  transport_correction   : 1 = extended transport correction of the Boltzmann
+ *                           moments, sigma_l - sigma_{N+1} (Sec. 3.3.1).
+ *  rank_mode, rank,       : truncation (Sec. 2.2). FIXED keeps min(rank, numerical rank);
+ *  rank_max, trunc_tol      ADAPTIVE keeps the smallest r with sum_{i>r} sigma_i <=
+ *                           trunc_tol * ||sigma||_2 clamped to [1, rank_max]; SCHEDULE
+ *                           replays rank_schedule. rank_max (<= 64) is the capacity.
+ *  rank_schedule          : SCHEDULE only; host array [n_energy_steps][2] of ranks after
+ *                           the streaming and the source truncation (-1 = none), copied
+ *                           by dlra_init.
+ *  e_max, e_min,          : uniform energy grid E_k = e_max - k dE (Sec. 3.3).
+ *  n_energy_steps
+ *  cfl_max                : streaming RK4 sub-steps per energy step are
+ *                           ceil(dE sum_d lam_max/delta_d / (min_x S(x,E_k) cfl_max)).
+ *  precision              : DLRA_FP64, or DLRA_FP32_MIXED (FP32 n-side data and
+ *                           arithmetic, FP64 reductions, factorisations and S).
+ *  bk_p, bk_alpha         : Bragg-Kleeman water stopping power S_w(E) = E^(1-p)/(p alpha).
+ *  t100                   : water scattering power at 100 MeV, T_w(E) = t100 (100/E)^2.
+ *  cuda_stream            : borrowed cudaStream_t for all work; NULL = legacy default.
+ */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  int32_t sh_degree;
+  int32_t collision;
+  int32_t transport_correction;
+  int32_t rank_mode, rank, rank_max;
+  double trunc_tol;
+  const int32_t* rank_schedule;
+  double e_max, e_min;
+  int32_t n_energy_steps;
+  double cfl_max;
+  int32_t precision;
+  double bk_p, bk_alpha, t100;
+  void* cuda_stream;
+} dlra_config;
+
+/* Base material of the mixture (Sec. 2.1, Eq. mixXS): density and ratios to water
+ * of the mass stopping power and mass scattering power, and the screening
+ * parameter eta of its screened-Rutherford kernel C/(1 - mu + 2 eta)^2. */
+typedef struct {
+  double density, sp_ratio, scatter_ratio, screening;
+} dlra_material;
+
+/* Pencil beam (Sec. 4): mean energy and Gaussian energy spread (MeV), a point on
+ * its axis and its direction, Gaussian spot sigma (cm) perpendicular to it, weight. */
+typedef struct {
+  double energy, energy_sigma;
+  double pos[3], dir[3];
+  double spot_sigma, weight;
+} dlra_beam;
+
+/* Create a context: validates cfg, builds the angular tables (A_x, A_y, A_z and
+ * |A_d|, Sec. 3.3.1-3.3.2) and allocates the low-rank state at capacity rank_max.
+ * *out receives the context; nothing is launched yet. */
+dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out);
+
+/* Set the mixture (Sec. 2.1): n_mat base materials and weights w [n_mat][n] (cell
+ * order of Sec. 3.3.2), w_m(x) >= 0 summing to 1 per cell. w may be host or device
+ * memory (w_on_device); it is copied. Computes the per-step physics tables and the
+ * streaming sub-step counts. Must precede dlra_add_beam. */
+dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material* mats,
+                               const double* w, int32_t w_on_device);
+
+/* Add a beam (independent low-rank state per beam): runs the CSDA ray tracer on
+ * the GPU (Sec. 3.2) for the bin-averaged uncollided fluence of every energy bin
+ * and the uncollided energy deposit. *beam_id receives its index. Must precede
+ * the first dlra_step. */
+dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id);
+
+/* Advance every beam by n_steps energy steps (Sec. 3.3.3), enqueued on the
+ * context's stream; returns after enqueueing unless an error is already latched.
+ * Fails with DLRA_ERR_STATE past the last energy step. */
+dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps);
+
+/* Dose e(x) = collided + uncollided deposited energy [MeV/cm^3] summed over beams,
+ * (per_mass = 1: divided by the density of the mixture, MeV/g). out [n] doubles,
+ * host or device memory. The collided part accumulates dE sqrt(4 pi) u_0(x) after
+ * every energy step. Synchronises the stream when out is a host pointer. */
+dlra_status dlra_dose(dlra_ctx* ctx, double* out, int32_t out_on_device, int32_t per_mass);
+
+/* Energy steps done so far (*step) and current rank of each beam (ranks[n_beams],
+ * may be NULL). Synchronises the stream. */
+dlra_status dlra_query(dlra_ctx* ctx, int32_t* step, int32_t* ranks);
+
+/* Ranks chosen by every truncation so far for one beam: log [n_energy_steps][2]
+ * (after streaming, after the source; -1 = no truncation). Synchronises. */
+dlra_status dlra_rank_log(dlra_ctx* ctx, int32_t beam_id, int32_t* log);
+
+/* Copy one beam's factors to host doubles: X [n][r] column-major n x r, S r x r
+ * column-major, W m x r column-major, *r the rank. Buffers must hold rank_max
+ * columns. Synchronises. */
+dlra_status dlra_get_state(dlra_ctx* ctx, int32_t beam_id, double* X, double* S, double* W, int32_t* r);
+
+/* Replace one beam's factors (host doubles, same layout as dlra_get_state;
+ * X and W must have orthonormal columns, 0 <= r <= rank_max). */
+dlra_status dlra_set_state(dlra_ctx* ctx, int32_t beam_id, const double* X, const double* S,
+                           const double* W, int32_t r);
+
+/* Copy the ray tracer's output of one beam to the host: the bin-averaged
+ * uncollided fluence of energy bin k (psi [n], 1/(cm^2 MeV)) and the uncollided
+ * deposit (e_u [n], MeV/cm^3); either pointer may be NULL. Synchronises. */
+dlra_status dlra_get_source(dlra_ctx* ctx, int32_t beam_id, int32_t k, double* psi, double* e_u);
+
+/* Copy the angular tables to the host, m x m row-major each: A [3][m][m] and
+ * absA [3][m][m] = |A_d| = V_d |Lambda_d| V_d^T. Either pointer may be NULL. */
+dlra_status dlra_get_tables(dlra_ctx* ctx, double* A, double* absA);
+
+/* Number of RK4 sub-steps of the streaming update of each energy step,
+ * nsub [n_energy_steps]. Available after dlra_set_materials. */
+dlra_status dlra_get_substeps(dlra_ctx* ctx, int32_t* nsub);
+
+/* Rewind to E_max for a new solve with the same phantom and beams: zeroes every
+ * low-rank state, dose and rank log; retrace = 1 reruns the ray tracer of every
+ * beam into its existing buffers. Enqueued on the context's stream; allocates nothing. */
+dlra_status dlra_reset(dlra_ctx* ctx, int32_t retrace);
+
+/* Per-kernel timing with CUDA events on the context's stream. enable = 1 records an
+ * event pair around every launch of the fused streaming-stage kernel (the K-step
+ * RK4 stage: stencil + r x r mix) until disabled; dlra_kernel_stats synchronises and
+ * returns the summed time in ms and the number of timed launches since enabling. */
+dlra_status dlra_set_profiling(dlra_ctx* ctx, int32_t enable);
+dlra_status dlra_kernel_stats(dlra_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Kernel launches issued by this context so far (for launch accounting). */
+int64_t dlra_launch_count(const dlra_ctx* ctx);
+
+/* One-line description of the last error of this context (never NULL). */
+const char* dlra_last_error(const dlra_ctx* ctx);
+
+/* Release every resource of the context (NULL is ignored). */
+void dlra_destroy(dlra_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DLRA_H */

@@ -22,7 +22,8 @@ Per voxel segment the energy follows from the water range, because every base
 material has the water energy dependence (S(x,E) = f(x) S_w(E)):
 R_w(E(s)) = R_w(E_in) - f (s - s_in). The particle weight and the fluence and
 deposit integrals are evaluated by nested Gauss-Legendre quadrature of their
-definitions in s.
+definitions, written in the energy variable (ds = dE / S(x, E)), which stays
+smooth up to the end of the range.
 
 Pins (tests/test_oracle_raytrace.py): homogeneous water, normal incidence: the
 closed form N(s) = exp(-int Sigma_t ds) with E(s) = ((R_0 - s)/alpha)^(1/p); the
@@ -148,6 +149,13 @@ def trace(prob, beam, nq: int = 12) -> RayTraceResult:
     xg, wg = np.polynomial.legendre.leggauss(nq)
     V = prob.volume
 
+    def stopping_cell(cell, E):
+        """S(x, E) = sum_i w_i(x) S_i(E) (Eq. mixXS)."""
+        out = np.zeros(np.shape(E))
+        for i in range(prob.M):
+            out = out + prob.w[i, cell] * prob.phys.stopping_power(i, E)
+        return out
+
     def sigma_t_vec(cell, E):
         """Sigma_t(x, E) = sum_i w_i(x) Sigma_{t,i}(E) (Eq. mixXS)."""
         out = np.zeros(np.shape(E))
@@ -182,34 +190,26 @@ def trace(prob, beam, nq: int = 12) -> RayTraceResult:
             for sa, sb in zip(cuts[:-1], cuts[1:]):
                 if sb - sa <= 0.0:
                     continue
-                Ra = R - f * sa
-                Ea = physics.energy_from_range_water(Ra, p, alpha)
-                Emid = physics.energy_from_range_water(R - f * 0.5 * (sa + sb), p, alpha)
-                kbin = int(np.searchsorted(-prob.E, -Emid) - 1)
+                Ehi = float(physics.energy_from_range_water(R - f * sa, p, alpha))
+                Elo = float(physics.energy_from_range_water(R - f * sb, p, alpha))
+                kbin = int(np.searchsorted(-prob.E, -0.5 * (Ehi + Elo)) - 1)
                 kbin = min(max(kbin, 0), prob.K - 1)
-                # nodes in s on [sa, sb]
-                s = 0.5 * (sb - sa) * xg + 0.5 * (sb + sa)
-                ws = 0.5 * (sb - sa) * wg
-                Es = physics.energy_from_range_water(R - f * s, p, alpha)
-                # N(s) = N(sa) exp(-int_sa^s Sigma_t ds'), inner GL per node
-                Ns = np.empty(nq)
+                # integrals over the sub-segment written in the energy variable, ds = dE / S(x, E)
+                E = 0.5 * (Ehi - Elo) * xg + 0.5 * (Ehi + Elo)
+                wE = 0.5 * (Ehi - Elo) * wg
+                Sx = stopping_cell(cell, E)
+                NE = np.empty(nq)
                 for j in range(nq):
-                    si = 0.5 * (s[j] - sa) * xg + 0.5 * (s[j] + sa)
-                    wi = 0.5 * (s[j] - sa) * wg
-                    Ei = physics.energy_from_range_water(R - f * si, p, alpha)
-                    Ns[j] = N * math.exp(-np.sum(wi * sigma_t_vec(cell, Ei)))
-                st = sigma_t_vec(cell, Es)
-                Ssx = f * physics.stopping_power_water(Es, p, alpha)
-                int_N = np.sum(ws * Ns)
-                res.psi[kbin, cell] += wr * int_N / (V * prob.h)
-                res.e_u[cell] += wr * np.sum(ws * Ns * Ssx) / V
-                res.removed_energy += wr * np.sum(ws * st * Ns * Es)
-                res.removed_particles += wr * np.sum(ws * st * Ns)
-                # advance N to sb
-                sfull = 0.5 * (sb - sa) * xg + 0.5 * (sb + sa)
-                Efull = physics.energy_from_range_water(R - f * sfull, p, alpha)
-                N = N * math.exp(-np.sum(ws * sigma_t_vec(cell, Efull)))
-                del Ea
+                    # N(E) = N(Ehi) exp(-int_E^Ehi Sigma_t / S dE')
+                    Ei = 0.5 * (Ehi - E[j]) * xg + 0.5 * (Ehi + E[j])
+                    wi = 0.5 * (Ehi - E[j]) * wg
+                    NE[j] = N * math.exp(-np.sum(wi * sigma_t_vec(cell, Ei) / stopping_cell(cell, Ei)))
+                st = sigma_t_vec(cell, E)
+                res.psi[kbin, cell] += wr * np.sum(wE * NE / Sx) / (V * prob.h)
+                res.e_u[cell] += wr * np.sum(wE * NE) / V
+                res.removed_energy += wr * np.sum(wE * st * NE * E / Sx)
+                res.removed_particles += wr * np.sum(wE * st * NE / Sx)
+                N = N * math.exp(-np.sum(wE * st / Sx))
             R = Rb
             if stop:
                 res.cutoff_energy += wr * N * Emin

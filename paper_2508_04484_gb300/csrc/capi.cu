@@ -1,0 +1,1213 @@
+// C ABI and energy-step driver of the GB300 low-rank collided-proton transport
+// library (arXiv 2508.04484). Every step of the method runs in the kernels of
+// device.cuh, small.cu and raytrace.cu; this file owns the device state, builds
+// the per-energy tables and enqueues one energy step (Sec. 3.3.3) per beam:
+//
+//   streaming (augmented BUG, Sec. 2.2, Eq. KLS; RK4 in Horner form)
+//     P_k = W^T A^s_d W, G_k = X^T D^s_d rho^-1 X      (k = 2 d + s)
+//     K' = sum_k D_k(rho^-1 K) P_k c(t)                  (n-side, fused stencil x mix)
+//     L' = sum_k A^s_d L G_k^T c(t)                      (m-side)
+//     X^ = [X, orth((I - X X^T) K1)], W^ = [W, orth((I - W W^T) L1)]
+//     S' = sum_k G^_k S P^_k c(t), then truncated SVD
+//   collided scattering (implicit Euler L-step at E_{k+1}, QR)
+//   first-collision source (augmented K/L/S with explicit Euler, truncated SVD)
+//   dose e_c += dE sqrt(4 pi) (X S W^T)(:, 0)
+//
+// The stopping power of the mixture is S(x, E) = rho_s(x) S_w(E): every base
+// material has the water energy dependence, so S^-1 = rho_s^-1 c(t) with the
+// scalar c(t) = 1/S_w(E(t)) folded into the Horner coefficients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dlra.h"
+#include "device.cuh"
+#include "kernels.h"
+#include "tables.h"
+
+using namespace dlra;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// small helper kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pstack_kernel(const double* __restrict__ P, int RB, int nk, T* __restrict__ Pst) {
+  // Pst[(c' * nk + k) * RB + c] = P_k[c'][c], P_k[a][b] at P[(k*RB + b)*RB + a]
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int tot = nk * RB * RB;
+  if (e >= tot) return;
+  int c = e % RB, row = e / RB;
+  int k = row % nk, cp = row / nk;
+  Pst[e] = T(P[((long long)k * RB + c) * RB + cp]);
+}
+
+__global__ void gt_kernel(const double* __restrict__ G, int RB, int nk, double* __restrict__ Gt) {
+  // Gt[(k*RB + c)*RB + a] = G_k[c][a] = G[(k*RB + a)*RB + c]
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int tot = nk * RB * RB;
+  if (e >= tot) return;
+  int a = e % RB, j = e / RB;
+  int k = j / RB, c = j % RB;
+  Gt[e] = G[((long long)k * RB + a) * RB + c];
+}
+
+template <typename T>
+__global__ void src_vec_kernel(const T* __restrict__ w, const double* __restrict__ psi, long long n, int M,
+                               T* __restrict__ A) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ps = psi[i];
+  for (int j = 0; j < M; ++j) A[(long long)j * n + i] = T((double)w[(long long)j * n + i] * ps);
+}
+
+template <typename T>
+__global__ void dose_kernel(const T* __restrict__ X, long long n, const double* __restrict__ S,
+                            const T* __restrict__ W, int m, int RB, const BeamDims* __restrict__ dims, double fac,
+                            double* __restrict__ e) {
+  __shared__ double v[64];
+  int r = dims->r < RB ? dims->r : RB;
+  for (int c = threadIdx.x; c < RB; c += blockDim.x) {
+    double s = 0.0;
+    if (c < r)
+      for (int j = 0; j < r; ++j) s += S[j * RB + c] * (double)W[(long long)j * m];
+    v[c] = s;
+  }
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < r; ++c) acc += (double)X[(long long)c * n + i] * v[c];
+    e[i] += fac * acc;
+  }
+}
+
+__global__ void bin_flags_kernel(const double* __restrict__ psi, long long n, int K, int* __restrict__ flags) {
+  int k = blockIdx.y;
+  int any = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (psi[(long long)k * n + i] != 0.0) any = 1;
+  any = __syncthreads_or(any);
+  if (any && threadIdx.x == 0) atomicOr(flags + k, 1);
+}
+
+template <typename T>
+__global__ void convert_kernel(const double* __restrict__ in, T* __restrict__ out, long long cnt) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = T(in[i]);
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T* __restrict__ in, double* __restrict__ out, long long cnt) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = (double)in[i];
+}
+
+__global__ void dose_total_kernel(const double* __restrict__ ec, const double* __restrict__ eu, long long n,
+                                  int first, double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (first ? 0.0 : out[i]) + ec[i] + eu[i];
+}
+
+__global__ void div_kernel(double* __restrict__ out, const double* __restrict__ rho, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rho[i] > 0.0 ? out[i] / rho[i] : 0.0;
+}
+
+inline unsigned nblk(long long cnt, int bs) { return (unsigned)((cnt + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------
+// launch helpers for the tiled product and the Gram reduction
+// ---------------------------------------------------------------------------
+template <typename T, int BK, class AL, class BL, class EP>
+void gemm(cudaStream_t st, long long rows, int N, int Q, AL al, BL bl, EP ep, int64_t& nl) {
+  if (rows <= 0 || N <= 0) return;
+  int BN = std::min(64, (N + 3) / 4 * 4);
+  int threads = 16 * (BN / 4);
+  dim3 grid((unsigned)((rows + GM_BM - 1) / GM_BM), (unsigned)((N + BN - 1) / BN));
+  size_t smem = (size_t)(BK * GM_BM + BK * BN) * sizeof(T);
+  gemm_kernel<T, BK, AL, BL, EP><<<grid, threads, smem, st>>>(rows, N, Q, al, bl, ep);
+  ++nl;
+}
+
+template <typename T, class F>
+void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int* adim, int acap, int ncols_j, F f,
+          double* out, long long ldo, int64_t& nl) {
+  if (rows <= 0 || acap <= 0 || ncols_j <= 0) return;
+  int gy = (acap + 63) / 64, gz = (ncols_j + 63) / 64;
+  long long want = (rows + GR_TC - 1) / GR_TC;
+  long long cap = std::max(1, 1216 / (gy * gz));
+  int gx = (int)std::max(1LL, std::min(want, cap));
+  gram_kernel<T, F><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  ++nl;
+}
+
+// ---------------------------------------------------------------------------
+// engine state
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Base {
+  virtual ~Base() {}
+};
+
+template <typename T>
+struct Beam {
+  T* X = nullptr;
+  T* W = nullptr;
+  double* S = nullptr;
+  BeamDims* dims = nullptr;
+  int* rank_log = nullptr;
+  double* psi = nullptr;
+  double* e_u = nullptr;
+  double* e_c = nullptr;
+  double* Bsrc = nullptr;
+  std::vector<int> has_src;
+  bool active = false;
+};
+
+}  // namespace
+
+struct dlra_ctx {
+  dlra_config cfg{};
+  std::vector<int32_t> schedule_host;
+  std::string err = "no error";
+  dlra_status poisoned = DLRA_OK;
+  cudaStream_t st = nullptr;
+  bool fp64 = true;
+  int n = 0, m = 0, N = 0, K = 0, M = 0, RB = 0, nk = 0, n2 = 0;
+  bool two_d = false;
+  Geo geo{};
+  AngularTables ang;
+  double h = 0.0;
+  std::vector<double> E;
+  std::vector<int> nsub;
+  int nsub_max = 1;
+  std::vector<dlra_material> mats;
+  std::vector<std::vector<double>> s_unit;
+  std::vector<double> xi_unit;
+  std::vector<double> rho_s_host, rho_host;
+  int step = 0;
+  bool materials_set = false;
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+  // type-erased engine buffers
+  void* beams = nullptr;   // std::vector<Beam<T>>*
+  // shared device buffers (raw pointers, typed at use)
+  void *inv_rho = nullptr, *wc = nullptr, *wT = nullptr, *Apm = nullptr;
+  void *Kb[3] = {nullptr, nullptr, nullptr}, *Xh = nullptr, *Asrc = nullptr;
+  void *Lb[3] = {nullptr, nullptr, nullptr}, *Zm = nullptr, *Wh = nullptr, *L1T = nullptr, *Pst = nullptr;
+  double *rho = nullptr, *f_cell = nullptr, *tau_cell = nullptr;
+  double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
+  double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr, *Gt = nullptr;
+  double *coef = nullptr, *sbeta = nullptr;
+  int* dev_err = nullptr;
+  int* schedule_dev = nullptr;
+  double* dose_tmp = nullptr;
+  // ray sets of the beams (for dlra_reset with retrace)
+  std::vector<double*> ray_dev;
+  std::vector<int> ray_count;
+  // streaming-stage kernel timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_count = 0;
+};
+
+namespace {
+
+dlra_status fail(dlra_ctx* c, dlra_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == DLRA_ERR_CUDA || s == DLRA_ERR_NONFINITE || s == DLRA_ERR_TIMEOUT) c->poisoned = s;
+  }
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? DLRA_ERR_OOM : DLRA_ERR_CUDA,      \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                            \
+  } while (0)
+
+dlra_status dalloc(dlra_ctx* ctx, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLRA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes, ctx->st);
+  if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+  return DLRA_OK;
+}
+
+#define ALLOC(ptr, bytes)                                                      \
+  do {                                                                         \
+    dlra_status s_ = dalloc(ctx, (void**)&(ptr), (size_t)(bytes));             \
+    if (s_ != DLRA_OK) return s_;                                              \
+  } while (0)
+
+double Sw(const dlra_ctx* c, double E) { return std::pow(E, 1.0 - c->cfg.bk_p) / (c->cfg.bk_p * c->cfg.bk_alpha); }
+double Tw(const dlra_ctx* c, double E) { return c->cfg.t100 * (100.0 / E) * (100.0 / E); }
+
+// G_{i,l} - Sigma_{t,i} (self-scattering) and G_{i,l} (in-scattering) at energy E.
+void moments_at(const dlra_ctx* c, int i, double E, std::vector<double>& self, std::vector<double>& src) {
+  const dlra_material& mt = c->mats[i];
+  const double xi1 = mt.density * mt.scatter_ratio * 0.5 * Tw(c, E);
+  self.assign(c->N + 1, 0.0);
+  src.assign(c->N + 1, 0.0);
+  if (c->cfg.collision == DLRA_BOLTZMANN) {
+    const double C = xi1 / c->xi_unit[i];
+    const std::vector<double>& s = c->s_unit[i];
+    const double corr = c->cfg.transport_correction ? s[c->N + 1] : 0.0;
+    for (int l = 0; l <= c->N; ++l) {
+      self[l] = C * (s[l] - s[0]);
+      src[l] = C * (s[l] - corr);
+    }
+  } else {
+    for (int l = 0; l <= c->N; ++l) {
+      self[l] = -0.5 * xi1 * l * (l + 1.0);
+      src[l] = self[l];
+    }
+  }
+}
+
+// Horner coefficients of one RK4 sub-step of y' = c(t) L y from pseudo-time t (energy Ea).
+void horner_betas(const dlra_ctx* c, double Ea, double hs, double* beta) {
+  const double c1 = 1.0 / Sw(c, Ea), c2 = 1.0 / Sw(c, Ea - 0.5 * hs), c4 = 1.0 / Sw(c, Ea - hs);
+  const double a1 = hs * (c1 + 4.0 * c2 + c4) / 6.0;
+  const double a2 = hs * hs * (c1 * c2 + c2 * c2 + c2 * c4) / 6.0;
+  const double a3 = hs * hs * hs * (c1 * c2 * c2 + c2 * c2 * c4) / 12.0;
+  const double a4 = hs * hs * hs * hs * c1 * c2 * c2 * c4 / 24.0;
+  beta[0] = a4 / a3;
+  beta[1] = a3 / a2;
+  beta[2] = a2 / a1;
+  beta[3] = a1;
+}
+
+// events around the streaming-stage kernel when profiling is on
+void prof_begin(dlra_ctx* c) {
+  if (!c->profiling) return;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int i = 0; i < 512; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used], c->st);
+}
+void prof_end(dlra_ctx* c) {
+  if (!c->profiling) return;
+  cudaEventRecord(c->ev_pool[c->ev_used + 1], c->st);
+  c->ev_used += 2;
+}
+void prof_collect(dlra_ctx* c) {
+  if (c->ev_used == 0) return;
+  cudaStreamSynchronize(c->st);
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]);
+    c->prof_ms += ms;
+    c->prof_count++;
+  }
+  c->ev_used = 0;
+}
+
+// ---------------------------------------------------------------------------
+// the energy step, templated on the n-side precision
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Engine {
+  dlra_ctx* ctx;
+  std::vector<Beam<T>>& beams() { return *reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams); }
+  T* P(void* p) { return reinterpret_cast<T*>(p); }
+
+  RankParams rank_params() {
+    RankParams rp;
+    rp.mode = ctx->cfg.rank_mode;
+    rp.rank = ctx->cfg.rank;
+    rp.rank_max = ctx->RB;
+    rp.tol = ctx->cfg.trunc_tol;
+    rp.nz_tol = sizeof(T) == 8 ? 1e-14 : 1e-6;
+    rp.cluster_tol = sizeof(T) == 8 ? 1e-10 : 1e-5;
+    rp.schedule = ctx->schedule_dev;
+    return rp;
+  }
+  double drop1() const { return sizeof(T) == 8 ? 1e-12 : 3e-4; }
+  double drop2() const { return sizeof(T) == 8 ? 1e-8 : 1e-3; }
+
+  // X^ = [X, orth((I - X X^T) K)] with K (n x qcap); X^ in ctx->Xh (n x 2RB)
+  void augment_x(Beam<T>& B, const T* K, int qcap) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB;
+    cudaStream_t st = ctx->st;
+    int64_t& nl = ctx->launches;
+    T* Xh = P(ctx->Xh);
+    cudaMemsetAsync(Xh + (long long)RB * n, 0, sizeof(T) * n * RB, st);
+    cudaMemcpyAsync(Xh, B.X, sizeof(T) * n * RB, cudaMemcpyDeviceToDevice, st);
+    const int* rdim = &B.dims->r;
+    // C1 = X^T K
+    cudaMemsetAsync(ctx->C1, 0, sizeof(double) * RB * qcap, st);
+    gram<T>(st, n, B.X, n, rdim, RB, qcap, FPlain<T>{K, n, nullptr, qcap}, ctx->C1, RB, nl);
+    // R = K - X C1 into X^[:, RB:RB+qcap]
+    gemm<T, 16>(st, n, qcap, RB, ALoadPlain<T>{B.X, n, rdim, RB},
+                BLoadCol<T, double>{ctx->C1, RB, nullptr, RB, nullptr, qcap},
+                EpiStore<T>{Xh + (long long)RB * n, n, K, n, T(-1), T(1)}, nl);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int lg = RB + qcap;
+      cudaMemsetAsync(ctx->Cg, 0, sizeof(double) * lg * qcap, st);
+      gram<T>(st, n, Xh, n, nullptr, lg, qcap, FPlain<T>{Xh + (long long)RB * n, n, nullptr, qcap}, ctx->Cg, lg, nl);
+      launch_orth_factor(st, ctx->Cg, pass == 0 ? ctx->C1 : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
+                         ctx->Mapply, &B.dims->qx, ctx->dev_err);
+      ++nl;
+      gemm<T, 16>(st, n, qcap, lg, ALoadPlain<T>{Xh, n, nullptr, lg},
+                  BLoadCol<T, double>{ctx->Mapply, lg, nullptr, lg, nullptr, qcap},
+                  EpiStore<T>{Xh + (long long)RB * n, n, nullptr, n, T(1), T(0)}, nl);
+    }
+  }
+
+  // X = X^ Pt, W = W^ Qt after a truncation
+  void apply_truncation(Beam<T>& B) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, n2 = ctx->n2, m = ctx->m;
+    int64_t& nl = ctx->launches;
+    gemm<T, 16>(ctx->st, n, RB, n2, ALoadPlain<T>{P(ctx->Xh), n, nullptr, n2},
+                BLoadCol<T, double>{ctx->Pt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.X, n, nullptr, n, T(1), T(0)},
+                nl);
+    gemm<T, 16>(ctx->st, m, RB, n2, ALoadPlain<T>{P(ctx->Wh), m, nullptr, n2},
+                BLoadCol<T, double>{ctx->Qt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.W, m, nullptr, m, T(1), T(0)},
+                nl);
+  }
+
+  void streaming(Beam<T>& B, int k) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, m = ctx->m, nk = ctx->nk, n2 = ctx->n2;
+    cudaStream_t st = ctx->st;
+    int64_t& nl = ctx->launches;
+    const int* rdim = &B.dims->r;
+    T* Zm = P(ctx->Zm);
+    // P_k = W^T A^s_d W
+    gemm<T, 16>(st, (long long)nk * m, RB, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
+                BLoadCol<T, T>{B.W, m, nullptr, m, rdim, RB}, EpiStoreKBlocks<T>{Zm, m, RB}, nl);
+    cudaMemsetAsync(ctx->P1, 0, sizeof(double) * nk * RB * RB, st);
+    gram<T>(st, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, ctx->P1, RB, nl);
+    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->P1, RB, nk, P(ctx->Pst));
+    ++nl;
+    // G_k = X^T D_k rho^-1 X
+    cudaMemsetAsync(ctx->G1, 0, sizeof(double) * nk * RB * RB, st);
+    gram<T>(st, n, B.X, n, rdim, RB, nk * RB, FStencil<T>{B.X, n, P(ctx->inv_rho), ctx->geo, RB, rdim}, ctx->G1, RB,
+            nl);
+    gt_kernel<<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->G1, RB, nk, ctx->Gt);
+    ++nl;
+    // K-step: K0 = X S, RK4 Horner stages z <- y + beta L(z)
+    T* y = P(ctx->Kb[0]);
+    T* za = P(ctx->Kb[1]);
+    T* zb = P(ctx->Kb[2]);
+    gemm<T, 16>(st, n, RB, RB, ALoadPlain<T>{B.X, n, rdim, RB}, BLoadCol<T, double>{B.S, RB, nullptr, RB, nullptr, RB},
+                EpiStore<T>{y, n, nullptr, n, T(1), T(0)}, nl);
+    // L-step: L0 = W S^T
+    T* ly = P(ctx->Lb[0]);
+    T* la = P(ctx->Lb[1]);
+    T* lb = P(ctx->Lb[2]);
+    gemm<T, 16>(st, m, RB, RB, ALoadPlain<T>{B.W, m, rdim, RB}, BLoadRow<T, double>{B.S, RB, RB, RB},
+                EpiStore<T>{ly, m, nullptr, m, T(1), T(0)}, nl);
+    const int ns = ctx->nsub[k];
+    const double hs = ctx->h / ns;
+    for (int j = 0; j < ns; ++j) {
+      double beta[4];
+      horner_betas(ctx, ctx->E[k] - j * hs, hs, beta);
+      const T* zin = y;
+      T* outs[4] = {za, zb, za, y};
+      const T* lin = ly;
+      T* louts[4] = {la, lb, la, ly};
+      for (int s = 0; s < 4; ++s) {
+        prof_begin(ctx);
+        gemm<T, 24>(st, n, RB, nk * RB, ALoadStencil<T>{zin, n, P(ctx->inv_rho), ctx->geo, rdim, RB},
+                    BLoadRow<T, T>{P(ctx->Pst), RB, nk * RB, RB}, EpiKStage<T>{outs[s], y, n, T(beta[s])}, nl);
+        prof_end(ctx);
+        zin = outs[s];
+        // m-side: Z_k = z G_k^T, out = y + beta sum_k A^s_d Z_k
+        gemm<T, 16>(st, m, nk * RB, RB, ALoadPlain<T>{lin, m, rdim, RB},
+                    BLoadCol<T, double>{ctx->Gt, RB, nullptr, RB, nullptr, nk * RB},
+                    EpiStore<T>{Zm, m, nullptr, m, T(1), T(0)}, nl);
+        gemm<T, 16>(st, m, RB, nk * m, ALoadRowBlocks<T>{P(ctx->Apm), m, nk}, BLoadKBlocks<T>{Zm, m, RB, nk},
+                    EpiKStage<T>{louts[s], ly, m, T(beta[s])}, nl);
+        lin = louts[s];
+      }
+    }
+    // augmentation of both bases
+    augment_x(B, y, RB);
+    launch_waug<T, T>(st, B.W, m, RB, ly, m, RB, drop1(), P(ctx->Wh), B.dims);
+    ++nl;
+    // Galerkin operators on the augmented bases
+    T* Xh = P(ctx->Xh);
+    T* Wh = P(ctx->Wh);
+    cudaMemsetAsync(ctx->Gc, 0, sizeof(double) * nk * n2 * n2, st);
+    gram<T>(st, n, Xh, n, nullptr, n2, nk * n2, FStencil<T>{Xh, n, P(ctx->inv_rho), ctx->geo, n2, nullptr}, ctx->Gc,
+            n2, nl);
+    gemm<T, 16>(st, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
+                BLoadCol<T, T>{Wh, m, nullptr, m, nullptr, n2}, EpiStoreKBlocks<T>{Zm, m, n2}, nl);
+    cudaMemsetAsync(ctx->Ph, 0, sizeof(double) * nk * n2 * n2, st);
+    gram<T>(st, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, ctx->Ph, n2, nl);
+    launch_sstep<T>(st, ctx->Gc, ctx->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, ctx->Sh);
+    ++nl;
+    launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 0, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
+                           ctx->dev_err);
+    ++nl;
+    apply_truncation(B);
+  }
+
+  void scattering(Beam<T>& B, int k) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, m = ctx->m, M = ctx->M, N = ctx->N;
+    cudaStream_t st = ctx->st;
+    int64_t& nl = ctx->launches;
+    const int* rdim = &B.dims->r;
+    cudaMemsetAsync(ctx->Mg, 0, sizeof(double) * M * RB * RB, st);
+    gram<T>(st, n, B.X, n, rdim, RB, M * RB, FDiag<T>{B.X, n, P(ctx->wc), n, RB, rdim, M}, ctx->Mg, RB, nl);
+    launch_scatter_solve<T>(st, ctx->Mg, M, ctx->coef + (long long)k * M * (N + 1), N, B.S, B.W, m, RB,
+                            P(ctx->L1T), ctx->dev_err);
+    ++nl;
+    launch_qr_lt<T>(st, P(ctx->L1T), m, RB, B.dims, B.W, B.S);
+    ++nl;
+  }
+
+  void source(Beam<T>& B, int k) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, m = ctx->m, M = ctx->M, n2 = ctx->n2;
+    cudaStream_t st = ctx->st;
+    int64_t& nl = ctx->launches;
+    T* A = P(ctx->Asrc);
+    src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), B.psi + (long long)k * n, n, M, A);
+    ++nl;
+    augment_x(B, A, M);
+    const double* Bk = B.Bsrc + (long long)k * M * m;
+    launch_waug<T, double>(st, B.W, m, RB, Bk, m, M, drop1(), P(ctx->Wh), B.dims);
+    ++nl;
+    cudaMemsetAsync(ctx->XA, 0, sizeof(double) * n2 * M, st);
+    gram<T>(st, n, P(ctx->Xh), n, nullptr, n2, M, FPlain<T>{A, n, nullptr, M}, ctx->XA, n2, nl);
+    launch_src_assemble<T>(st, B.S, RB, ctx->XA, Bk, P(ctx->Wh), m, M, n2, ctx->h, ctx->Sh);
+    ++nl;
+    launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 1, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
+                           ctx->dev_err);
+    ++nl;
+    apply_truncation(B);
+  }
+
+  void dose(Beam<T>& B) {
+    dose_kernel<T><<<std::min<unsigned>(nblk(ctx->n, 256), 2048), 256, 0, ctx->st>>>(
+        B.X, ctx->n, B.S, B.W, ctx->m, ctx->RB, B.dims, ctx->h * std::sqrt(4.0 * M_PI), B.e_c);
+    ++ctx->launches;
+  }
+
+  dlra_status step_all(int nsteps) {
+    for (int s = 0; s < nsteps; ++s) {
+      const int k = ctx->step;
+      for (auto& B : beams()) {
+        if (B.active) {
+          streaming(B, k);
+          scattering(B, k);
+        }
+        if (B.has_src[k]) {
+          source(B, k);
+          B.active = true;
+        }
+        if (B.active) dose(B);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "kernel launch failed at step %d: %s", k, cudaGetErrorString(e));
+      ctx->step++;
+      if (ctx->ev_used > 4096) prof_collect(ctx);
+    }
+    return DLRA_OK;
+  }
+};
+
+dlra_status check_device_errors(dlra_ctx* ctx) {
+  if (ctx->poisoned != DLRA_OK) return ctx->poisoned;
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "stream failed: %s", cudaGetErrorString(e));
+  int h = 0;
+  e = cudaMemcpy(&h, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "error flag read failed: %s", cudaGetErrorString(e));
+  if (h & ERR_NONFINITE) return fail(ctx, DLRA_ERR_NONFINITE, "the low-rank state became non-finite");
+  if (h & ERR_CHOLESKY) return fail(ctx, DLRA_ERR_NONFINITE, "implicit scattering matrix is not positive definite");
+  if (h & ERR_CAPACITY) return fail(ctx, DLRA_ERR_RANK, "rank capacity rank_max exceeded");
+  return DLRA_OK;
+}
+
+template <typename T>
+std::vector<Beam<T>>& beams_of(dlra_ctx* ctx) {
+  return *reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams);
+}
+
+template <typename T>
+dlra_status alloc_shared(dlra_ctx* ctx) {
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB, nk = ctx->nk, n2 = ctx->n2;
+  ALLOC(ctx->inv_rho, sizeof(T) * n);
+  ALLOC(ctx->rho, sizeof(double) * n);
+  ALLOC(ctx->f_cell, sizeof(double) * n);
+  ALLOC(ctx->tau_cell, sizeof(double) * n);
+  for (int i = 0; i < 3; ++i) ALLOC(ctx->Kb[i], sizeof(T) * n * RB);
+  ALLOC(ctx->Xh, sizeof(T) * n * n2);
+  for (int i = 0; i < 3; ++i) ALLOC(ctx->Lb[i], sizeof(T) * m * RB);
+  ALLOC(ctx->Zm, sizeof(T) * (size_t)m * nk * n2);
+  ALLOC(ctx->Wh, sizeof(T) * (size_t)m * n2);
+  ALLOC(ctx->L1T, sizeof(T) * (size_t)m * RB);
+  ALLOC(ctx->Pst, sizeof(T) * (size_t)nk * RB * RB);
+  ALLOC(ctx->Apm, sizeof(T) * (size_t)nk * m * m);
+  ALLOC(ctx->G1, sizeof(double) * nk * RB * RB);
+  ALLOC(ctx->P1, sizeof(double) * nk * RB * RB);
+  ALLOC(ctx->Gt, sizeof(double) * nk * RB * RB);
+  ALLOC(ctx->Gc, sizeof(double) * nk * n2 * n2);
+  ALLOC(ctx->Ph, sizeof(double) * nk * n2 * n2);
+  ALLOC(ctx->C1, sizeof(double) * RB * RB);
+  ALLOC(ctx->Cg, sizeof(double) * n2 * RB);
+  ALLOC(ctx->Mapply, sizeof(double) * n2 * RB);
+  ALLOC(ctx->Sh, sizeof(double) * n2 * n2);
+  ALLOC(ctx->Pt, sizeof(double) * n2 * RB);
+  ALLOC(ctx->Qt, sizeof(double) * n2 * RB);
+  ALLOC(ctx->dev_err, sizeof(int));
+  ALLOC(ctx->dose_tmp, sizeof(double) * n);
+  return DLRA_OK;
+}
+
+template <typename T>
+dlra_status upload_apm(dlra_ctx* ctx) {
+  // A^+_d = (A_d + |A_d|)/2 (s = 0) and A^-_d = (A_d - |A_d|)/2 (s = 1), row-major per k
+  const int m = ctx->m;
+  std::vector<T> h((size_t)ctx->nk * m * m);
+  for (int da = 0; da < ctx->geo.nact; ++da) {
+    const int d = ctx->geo.dirs[da];
+    for (int s = 0; s < 2; ++s)
+      for (int p = 0; p < m; ++p)
+        for (int q = 0; q < m; ++q) {
+          double a = ctx->ang.A[d][(size_t)p * m + q], b = ctx->ang.absA[d][(size_t)p * m + q];
+          h[((size_t)(2 * da + s) * m + p) * m + q] = T(0.5 * (s == 0 ? a + b : a - b));
+        }
+  }
+  CK(cudaMemcpyAsync(ctx->Apm, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return DLRA_OK;
+}
+
+template <typename T>
+dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
+  const long long n = ctx->n;
+  const int M = ctx->M;
+  // mixture: S(x, E) = rho_s(x) S_w(E), rho_s = sum_i w_i rho_i s_i
+  std::vector<double> rho_s(n, 0.0), rho(n, 0.0), tau(n, 0.0);
+  std::vector<T> inv_rho(n), wc((size_t)M * n), wT((size_t)M * n);
+  for (int i = 0; i < M; ++i) {
+    const dlra_material& mt = ctx->mats[i];
+    double g0 = 0.0;
+    if (ctx->cfg.collision == DLRA_BOLTZMANN) {
+      const std::vector<double>& s = ctx->s_unit[i];
+      g0 = (s[0] - (ctx->cfg.transport_correction ? s[ctx->N + 1] : 0.0)) / ctx->xi_unit[i];
+    }
+    for (long long x = 0; x < n; ++x) {
+      double wv = w_host[(size_t)i * n + x];
+      rho_s[x] += wv * mt.density * mt.sp_ratio;
+      rho[x] += wv * mt.density;
+      tau[x] += wv * mt.density * mt.scatter_ratio * g0;
+    }
+  }
+  double rmin = 1e300;
+  for (long long x = 0; x < n; ++x) {
+    if (!(rho_s[x] > 0.0)) return fail(ctx, DLRA_ERR_ARG, "cell %lld has no stopping power (rho_s = %g)", x, rho_s[x]);
+    rmin = std::min(rmin, rho_s[x]);
+    inv_rho[x] = T(1.0 / rho_s[x]);
+  }
+  for (int i = 0; i < M; ++i)
+    for (long long x = 0; x < n; ++x) {
+      wc[(size_t)i * n + x] = T(w_host[(size_t)i * n + x] / rho_s[x]);
+      wT[(size_t)i * n + x] = T(w_host[(size_t)i * n + x]);
+    }
+  ctx->rho_s_host = rho_s;
+  ctx->rho_host = rho;
+  ALLOC(ctx->wc, sizeof(T) * M * n);
+  ALLOC(ctx->wT, sizeof(T) * M * n);
+  ALLOC(ctx->Asrc, sizeof(T) * M * n);
+  ALLOC(ctx->Mg, sizeof(double) * M * ctx->RB * ctx->RB);
+  ALLOC(ctx->XA, sizeof(double) * ctx->n2 * M);
+  CK(cudaMemcpyAsync(ctx->inv_rho, inv_rho.data(), sizeof(T) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->wc, wc.data(), sizeof(T) * wc.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->wT, wT.data(), sizeof(T) * wT.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->rho, rho.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->f_cell, rho_s.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->tau_cell, tau.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  // sub-steps, Horner coefficients, scattering coefficients per energy step
+  const int K = ctx->K;
+  double lam = 0.0;
+  for (int da = 0; da < ctx->geo.nact; ++da) {
+    int d = ctx->geo.dirs[da];
+    double delta = d == 0 ? ctx->cfg.dx : (d == 1 ? ctx->cfg.dy : ctx->cfg.dz);
+    lam += ctx->ang.lam_max / delta;
+  }
+  ctx->nsub.assign(K, 1);
+  for (int k = 0; k < K; ++k) {
+    double nu = ctx->h * lam / (rmin * Sw(ctx, ctx->E[k]) * ctx->cfg.cfl_max);
+    ctx->nsub[k] = std::max(1, (int)std::ceil(nu - 1e-9));
+  }
+  ctx->nsub_max = *std::max_element(ctx->nsub.begin(), ctx->nsub.end());
+  std::vector<double> sbeta((size_t)K * ctx->nsub_max * 4, 0.0);
+  for (int k = 0; k < K; ++k) {
+    double hs = ctx->h / ctx->nsub[k];
+    for (int j = 0; j < ctx->nsub[k]; ++j) horner_betas(ctx, ctx->E[k] - j * hs, hs, &sbeta[((size_t)k * ctx->nsub_max + j) * 4]);
+  }
+  std::vector<double> coef((size_t)K * M * (ctx->N + 1));
+  std::vector<double> self, src;
+  for (int k = 0; k < K; ++k) {
+    double E1 = ctx->E[k + 1];
+    for (int i = 0; i < M; ++i) {
+      moments_at(ctx, i, E1, self, src);
+      for (int l = 0; l <= ctx->N; ++l) coef[((size_t)k * M + i) * (ctx->N + 1) + l] = ctx->h * self[l] / Sw(ctx, E1);
+    }
+  }
+  ALLOC(ctx->sbeta, sizeof(double) * sbeta.size());
+  ALLOC(ctx->coef, sizeof(double) * coef.size());
+  CK(cudaMemcpyAsync(ctx->sbeta, sbeta.data(), sizeof(double) * sbeta.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return DLRA_OK;
+}
+
+RayGeo ray_geo(const dlra_ctx* ctx) {
+  const dlra_config& c = ctx->cfg;
+  RayGeo g;
+  g.nx = c.nx; g.ny = c.ny; g.nz = c.nz; g.two_d = ctx->two_d ? 1 : 0; g.K = ctx->K;
+  g.dx = c.dx; g.dy = ctx->two_d ? 1.0 : c.dy; g.dz = c.dz;
+  g.e_max = c.e_max; g.h = ctx->h; g.e_min = c.e_min; g.p = c.bk_p; g.alpha = c.bk_alpha;
+  g.klam = c.t100 * 1e4 * c.bk_p * c.bk_alpha / 2.0;
+  g.volume = c.dx * c.dz * (ctx->two_d ? 1.0 : c.dy);
+  return g;
+}
+
+template <typename T>
+dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB, K = ctx->K, M = ctx->M;
+  const dlra_config& c = ctx->cfg;
+  // rays: transverse Gaussian grid at half-integer pitch, Gauss-Hermite energies
+  double d[3] = {b->dir[0], b->dir[1], b->dir[2]};
+  double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (!(dn > 0.0)) return fail(ctx, DLRA_ERR_ARG, "beam direction is zero");
+  for (double& v : d) v /= dn;
+  if (ctx->two_d && std::fabs(d[1]) > 1e-12) return fail(ctx, DLRA_ERR_ARG, "a 2-D slab beam must have dir[1] = 0");
+  double u1[3], u2[3] = {0, 0, 0};
+  if (ctx->two_d) {
+    double l = std::sqrt(d[2] * d[2] + d[0] * d[0]);
+    u1[0] = d[2] / l; u1[1] = 0.0; u1[2] = -d[0] / l;
+  } else {
+    double e[3] = {0, 1, 0};
+    if (std::fabs(d[1]) >= 0.9) { e[0] = 1; e[1] = 0; }
+    u1[0] = e[1] * d[2] - e[2] * d[1];
+    u1[1] = e[2] * d[0] - e[0] * d[2];
+    u1[2] = e[0] * d[1] - e[1] * d[0];
+    double l = std::sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    for (double& v : u1) v /= l;
+    u2[0] = d[1] * u1[2] - d[2] * u1[1];
+    u2[1] = d[2] * u1[0] - d[0] * u1[2];
+    u2[2] = d[0] * u1[1] - d[1] * u1[0];
+  }
+  double pitch = ctx->two_d ? std::min(c.dx, c.dz) / 4.0 : std::min(c.dx, std::min(c.dy, c.dz)) / 4.0;
+  std::vector<double> offs, gw;
+  if (b->spot_sigma > 0.0) {
+    int nh = (int)std::ceil(3.5 * b->spot_sigma / pitch);
+    for (int j = -nh; j < nh; ++j) {
+      double o = (j + 0.5) * pitch;
+      offs.push_back(o);
+      gw.push_back(std::exp(-0.5 * (o / b->spot_sigma) * (o / b->spot_sigma)));
+    }
+  } else {
+    offs.push_back(0.0);
+    gw.push_back(1.0);
+  }
+  std::vector<double> ee, ew;
+  if (b->energy_sigma > 0.0) {
+    double x[5], w[5];
+    gauss_hermite(5, x, w);
+    for (int i = 0; i < 5; ++i) {
+      ee.push_back(b->energy + std::sqrt(2.0) * b->energy_sigma * x[i]);
+      ew.push_back(w[i] / std::sqrt(M_PI));
+    }
+  } else {
+    ee.push_back(b->energy);
+    ew.push_back(1.0);
+  }
+  for (double e : ee)
+    if (e > c.e_max + 1e-12 || e <= c.e_min)
+      return fail(ctx, DLRA_ERR_ARG, "beam energy node %.6g outside (e_min, e_max]", e);
+  std::vector<double> rays;
+  double wsum = 0.0;
+  std::vector<std::pair<std::array<double, 3>, double>> pts;
+  if (ctx->two_d) {
+    for (size_t i = 0; i < offs.size(); ++i) {
+      std::array<double, 3> p = {b->pos[0] + offs[i] * u1[0], b->pos[1] + offs[i] * u1[1], b->pos[2] + offs[i] * u1[2]};
+      pts.push_back({p, gw[i]});
+      wsum += gw[i];
+    }
+  } else {
+    for (size_t i = 0; i < offs.size(); ++i)
+      for (size_t j = 0; j < offs.size(); ++j) {
+        std::array<double, 3> p;
+        for (int a = 0; a < 3; ++a) p[a] = b->pos[a] + offs[i] * u1[a] + offs[j] * u2[a];
+        pts.push_back({p, gw[i] * gw[j]});
+        wsum += gw[i] * gw[j];
+      }
+  }
+  for (auto& pt : pts)
+    for (size_t e = 0; e < ee.size(); ++e) {
+      rays.insert(rays.end(), {pt.first[0], pt.first[1], pt.first[2], d[0], d[1], d[2], ee[e],
+                               b->weight * pt.second / wsum * ew[e]});
+    }
+  const int nray = (int)(rays.size() / 8);
+  Beam<T> B;
+  ALLOC(B.X, sizeof(T) * n * RB);
+  ALLOC(B.W, sizeof(T) * (size_t)m * RB);
+  ALLOC(B.S, sizeof(double) * RB * RB);
+  ALLOC(B.dims, sizeof(BeamDims));
+  ALLOC(B.rank_log, sizeof(int) * 2 * K);
+  ALLOC(B.psi, sizeof(double) * (size_t)K * n);
+  ALLOC(B.e_u, sizeof(double) * n);
+  ALLOC(B.e_c, sizeof(double) * n);
+  ALLOC(B.Bsrc, sizeof(double) * (size_t)K * M * m);
+  {
+    std::vector<int> neg(2 * K, -1);
+    CK(cudaMemcpyAsync(B.rank_log, neg.data(), sizeof(int) * 2 * K, cudaMemcpyHostToDevice, ctx->st));
+  }
+  double* rays_dev = nullptr;
+  ALLOC(rays_dev, sizeof(double) * rays.size());
+  CK(cudaMemcpyAsync(rays_dev, rays.data(), sizeof(double) * rays.size(), cudaMemcpyHostToDevice, ctx->st));
+  RayGeo g = ray_geo(ctx);
+  ctx->ray_dev.push_back(rays_dev);
+  ctx->ray_count.push_back(nray);
+  launch_raytrace(ctx->st, rays_dev, nray, g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+  ++ctx->launches;
+  int* flags = nullptr;
+  ALLOC(flags, sizeof(int) * K);
+  bin_flags_kernel<<<dim3(std::min<unsigned>(nblk(n, 256), 64), K), 256, 0, ctx->st>>>(B.psi, n, K, flags);
+  ++ctx->launches;
+  B.has_src.assign(K, 0);
+  CK(cudaMemcpyAsync(B.has_src.data(), flags, sizeof(int) * K, cudaMemcpyDeviceToHost, ctx->st));
+  // in-scattering moment vectors B[k][i][p] = G_{i,l(p)}(E_{k+1/2}) m_p(Omega)
+  std::vector<double> mo(m), Bh((size_t)K * M * m), self, src;
+  real_sh_dir(ctx->N, d, mo.data());
+  for (int k = 0; k < K; ++k) {
+    double Em = 0.5 * (ctx->E[k] + ctx->E[k + 1]);
+    for (int i = 0; i < M; ++i) {
+      moments_at(ctx, i, Em, self, src);
+      for (int p = 0; p < m; ++p) Bh[((size_t)k * M + i) * m + p] = src[ctx->ang.degree[p]] * mo[p];
+    }
+  }
+  CK(cudaMemcpyAsync(B.Bsrc, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
+  beams_of<T>(ctx).push_back(B);
+  *id = (int32_t)beams_of<T>(ctx).size() - 1;
+  return DLRA_OK;
+}
+
+template <typename T>
+dlra_status get_state_t(dlra_ctx* ctx, int id, double* X, double* S, double* W, int32_t* r) {
+  Beam<T>& B = beams_of<T>(ctx)[id];
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB;
+  BeamDims dh;
+  CK(cudaMemcpy(&dh, B.dims, sizeof(BeamDims), cudaMemcpyDeviceToHost));
+  *r = dh.r;
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * std::max<long long>(n, m) * RB));
+  if (X) {
+    to_double_kernel<T><<<nblk(n * RB, 256), 256, 0, ctx->st>>>(B.X, tmp, n * RB);
+    CK(cudaMemcpyAsync(X, tmp, sizeof(double) * n * RB, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  if (W) {
+    to_double_kernel<T><<<nblk((long long)m * RB, 256), 256, 0, ctx->st>>>(B.W, tmp, (long long)m * RB);
+    CK(cudaMemcpyAsync(W, tmp, sizeof(double) * m * RB, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  if (S) CK(cudaMemcpy(S, B.S, sizeof(double) * RB * RB, cudaMemcpyDeviceToHost));
+  cudaFree(tmp);
+  return DLRA_OK;
+}
+
+template <typename T>
+dlra_status set_state_t(dlra_ctx* ctx, int id, const double* X, const double* S, const double* W, int r) {
+  Beam<T>& B = beams_of<T>(ctx)[id];
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB;
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * std::max<long long>(n, m) * RB));
+  std::vector<double> hx((size_t)std::max<long long>(n, m) * RB, 0.0);
+  for (long long c = 0; c < r; ++c)
+    for (long long i = 0; i < n; ++i) hx[c * n + i] = X[c * n + i];
+  CK(cudaMemcpy(tmp, hx.data(), sizeof(double) * n * RB, cudaMemcpyHostToDevice));
+  convert_kernel<T><<<nblk(n * RB, 256), 256, 0, ctx->st>>>(tmp, B.X, n * RB);
+  CK(cudaStreamSynchronize(ctx->st));
+  std::fill(hx.begin(), hx.end(), 0.0);
+  for (long long c = 0; c < r; ++c)
+    for (long long i = 0; i < m; ++i) hx[c * m + i] = W[c * m + i];
+  CK(cudaMemcpy(tmp, hx.data(), sizeof(double) * m * RB, cudaMemcpyHostToDevice));
+  convert_kernel<T><<<nblk((long long)m * RB, 256), 256, 0, ctx->st>>>(tmp, B.W, (long long)m * RB);
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<double> hs((size_t)RB * RB, 0.0);
+  for (int c = 0; c < r; ++c)
+    for (int a = 0; a < r; ++a) hs[(size_t)c * RB + a] = S[(size_t)c * RB + a];
+  CK(cudaMemcpy(B.S, hs.data(), sizeof(double) * RB * RB, cudaMemcpyHostToDevice));
+  BeamDims dh{r, 0, 0, 0};
+  CK(cudaMemcpy(B.dims, &dh, sizeof(BeamDims), cudaMemcpyHostToDevice));
+  B.active = r > 0;
+  cudaFree(tmp);
+  return DLRA_OK;
+}
+
+template <typename T>
+dlra_status dose_t(dlra_ctx* ctx, double* out, int on_device, int per_mass) {
+  const long long n = ctx->n;
+  auto& bs = beams_of<T>(ctx);
+  double* dst = on_device ? out : ctx->dose_tmp;
+  if (bs.empty()) CK(cudaMemsetAsync(dst, 0, sizeof(double) * n, ctx->st));
+  for (size_t b = 0; b < bs.size(); ++b)
+    dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[b].e_c, bs[b].e_u, n, b == 0 ? 1 : 0, dst);
+  if (per_mass) div_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(dst, ctx->rho, n);
+  CK(cudaGetLastError());
+  if (!on_device) {
+    CK(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return check_device_errors(ctx);
+}
+
+template <typename T>
+dlra_status reset_t(dlra_ctx* ctx, int retrace) {
+  const long long n = ctx->n;
+  auto& bs = beams_of<T>(ctx);
+  RayGeo g = ray_geo(ctx);
+  for (size_t b = 0; b < bs.size(); ++b) {
+    Beam<T>& B = bs[b];
+    CK(cudaMemsetAsync(B.dims, 0, sizeof(BeamDims), ctx->st));
+    CK(cudaMemsetAsync(B.e_c, 0, sizeof(double) * n, ctx->st));
+    CK(cudaMemsetAsync(B.S, 0, sizeof(double) * ctx->RB * ctx->RB, ctx->st));
+    CK(cudaMemsetAsync(B.rank_log, 0xff, sizeof(int) * 2 * ctx->K, ctx->st));
+    if (retrace) {
+      CK(cudaMemsetAsync(B.psi, 0, sizeof(double) * (size_t)ctx->K * n, ctx->st));
+      CK(cudaMemsetAsync(B.e_u, 0, sizeof(double) * n, ctx->st));
+      launch_raytrace(ctx->st, ctx->ray_dev[b], ctx->ray_count[b], g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+      ++ctx->launches;
+    }
+    B.active = false;
+  }
+  CK(cudaGetLastError());
+  ctx->step = 0;
+  return DLRA_OK;
+}
+
+template <typename T>
+void free_beams(dlra_ctx* ctx) {
+  delete reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams);
+  ctx->beams = nullptr;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
+  if (!cfg || !out) return DLRA_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<dlra_ctx> c(new dlra_ctx());
+  dlra_ctx* ctx = c.get();
+  ctx->cfg = *cfg;
+  const dlra_config& g = *cfg;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(ctx, DLRA_ERR_ARG, "grid sizes must be >= 1");
+  ctx->two_d = (g.ny == 1 && g.dy == 0.0);
+  if (!(g.dx > 0 && g.dz > 0 && (ctx->two_d || g.dy > 0))) return fail(ctx, DLRA_ERR_ARG, "voxel sizes must be > 0");
+  if (g.sh_degree < 1 || g.sh_degree > 31) return fail(ctx, DLRA_ERR_ARG, "sh_degree must be in [1, 31]");
+  if (g.collision != DLRA_FOKKER_PLANCK && g.collision != DLRA_BOLTZMANN) return fail(ctx, DLRA_ERR_ARG, "bad collision");
+  if (g.rank_mode < 0 || g.rank_mode > 2) return fail(ctx, DLRA_ERR_ARG, "bad rank_mode");
+  if (g.precision != DLRA_FP64 && g.precision != DLRA_FP32_MIXED) return fail(ctx, DLRA_ERR_ARG, "bad precision");
+  if (g.rank_max < 1 || g.rank_max > 64) return fail(ctx, DLRA_ERR_ARG, "rank_max must be in [1, 64]");
+  if (g.rank_mode == DLRA_RANK_FIXED && (g.rank < 1 || g.rank > g.rank_max))
+    return fail(ctx, DLRA_ERR_ARG, "rank must be in [1, rank_max]");
+  if (g.rank_mode == DLRA_RANK_ADAPTIVE && !(g.trunc_tol > 0)) return fail(ctx, DLRA_ERR_ARG, "trunc_tol must be > 0");
+  if (g.n_energy_steps < 1 || !(g.e_max > g.e_min) || !(g.e_min > 0))
+    return fail(ctx, DLRA_ERR_ARG, "need e_max > e_min > 0 and n_energy_steps >= 1");
+  if (!(g.cfl_max > 0)) return fail(ctx, DLRA_ERR_ARG, "cfl_max must be > 0");
+  if (!(g.bk_p > 1 && g.bk_p < 2 && g.bk_alpha > 0 && g.t100 >= 0))
+    return fail(ctx, DLRA_ERR_ARG, "need 1 < bk_p < 2, bk_alpha > 0, t100 >= 0");
+  ctx->fp64 = g.precision == DLRA_FP64;
+  if (ctx->fp64 && g.rank_max > 32) return fail(ctx, DLRA_ERR_ARG, "FP64 precision supports rank_max <= 32");
+  ctx->st = (cudaStream_t)g.cuda_stream;
+  ctx->n = g.nx * g.ny * g.nz;
+  ctx->N = g.sh_degree;
+  ctx->m = (g.sh_degree + 1) * (g.sh_degree + 1);
+  ctx->K = g.n_energy_steps;
+  ctx->RB = (g.rank_max + 3) / 4 * 4;
+  if (ctx->RB > 64) ctx->RB = 64;
+  ctx->n2 = 2 * ctx->RB;
+  const size_t tsz = ctx->fp64 ? 8 : 4;
+  if ((size_t)ctx->m * ctx->RB * tsz > 160 * 1024)
+    return fail(ctx, DLRA_ERR_ARG, "m * rank_max too large for the one-block QR (m=%d)", ctx->m);
+  if (g.rank_mode == DLRA_RANK_SCHEDULE) {
+    if (!g.rank_schedule) return fail(ctx, DLRA_ERR_ARG, "SCHEDULE mode needs rank_schedule");
+    ctx->schedule_host.assign(g.rank_schedule, g.rank_schedule + 2 * ctx->K);
+  }
+  ctx->cfg.rank_schedule = nullptr;
+  ctx->geo.nx = g.nx;
+  ctx->geo.ny = g.ny;
+  ctx->geo.nz = g.nz;
+  ctx->geo.nxy = (long long)g.nx * g.ny;
+  ctx->geo.n = ctx->n;
+  if (ctx->two_d) {
+    ctx->geo.nact = 2;
+    ctx->geo.dirs[0] = 0;
+    ctx->geo.dirs[1] = 2;
+    ctx->geo.dirs[2] = 2;
+  } else {
+    ctx->geo.nact = 3;
+    for (int i = 0; i < 3; ++i) ctx->geo.dirs[i] = i;
+  }
+  ctx->geo.inv2d[0] = 1.0 / (2.0 * g.dx);
+  ctx->geo.inv2d[1] = ctx->two_d ? 0.0 : 1.0 / (2.0 * g.dy);
+  ctx->geo.inv2d[2] = 1.0 / (2.0 * g.dz);
+  ctx->nk = 2 * ctx->geo.nact;
+  ctx->h = (g.e_max - g.e_min) / g.n_energy_steps;
+  ctx->E.resize(ctx->K + 1);
+  for (int k = 0; k <= ctx->K; ++k) ctx->E[k] = g.e_max - ctx->h * k;
+  char msg[256];
+  if (!build_angular(ctx->N, ctx->ang, msg, sizeof msg)) return fail(ctx, DLRA_ERR_ARG, "%s", msg);
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+    cudaGetLastError();
+    return fail(ctx, DLRA_ERR_CUDA, "no CUDA device");
+  }
+  dlra_status s;
+  if (ctx->fp64) {
+    ctx->beams = new std::vector<Beam<double>>();
+    s = alloc_shared<double>(ctx);
+    if (s == DLRA_OK) s = upload_apm<double>(ctx);
+  } else {
+    ctx->beams = new std::vector<Beam<float>>();
+    s = alloc_shared<float>(ctx);
+    if (s == DLRA_OK) s = upload_apm<float>(ctx);
+  }
+  if (s != DLRA_OK) {
+    *out = c.release();
+    return s;
+  }
+  if (!ctx->schedule_host.empty()) {
+    ALLOC(ctx->schedule_dev, sizeof(int) * ctx->schedule_host.size());
+    CK(cudaMemcpy(ctx->schedule_dev, ctx->schedule_host.data(), sizeof(int) * ctx->schedule_host.size(),
+                  cudaMemcpyHostToDevice));
+  }
+  *out = c.release();
+  return DLRA_OK;
+}
+
+dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material* mats, const double* w,
+                               int32_t w_on_device) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "materials already set");
+  if (n_mat < 1 || !mats || !w) return fail(ctx, DLRA_ERR_ARG, "need n_mat >= 1, mats and w");
+  if (n_mat > ctx->RB) return fail(ctx, DLRA_ERR_ARG, "n_mat must not exceed the rank capacity");
+  for (int i = 0; i < n_mat; ++i) {
+    const dlra_material& mt = mats[i];
+    if (!(mt.density > 0 && mt.sp_ratio > 0 && mt.scatter_ratio >= 0 && mt.screening > 0))
+      return fail(ctx, DLRA_ERR_ARG, "material %d: need density, sp_ratio, screening > 0", i);
+  }
+  ctx->M = n_mat;
+  ctx->mats.assign(mats, mats + n_mat);
+  ctx->s_unit.assign(n_mat, std::vector<double>(ctx->N + 2));
+  ctx->xi_unit.assign(n_mat, 0.0);
+  for (int i = 0; i < n_mat; ++i) screened_rutherford_moments(mats[i].screening, ctx->N + 1, ctx->s_unit[i].data(), &ctx->xi_unit[i]);
+  std::vector<double> wh;
+  const double* w_host = w;
+  if (w_on_device) {
+    wh.resize((size_t)n_mat * ctx->n);
+    CK(cudaMemcpy(wh.data(), w, sizeof(double) * wh.size(), cudaMemcpyDeviceToHost));
+    w_host = wh.data();
+  }
+  for (size_t i = 0; i < (size_t)n_mat * ctx->n; ++i)
+    if (!(w_host[i] >= 0.0) || std::isinf(w_host[i])) return fail(ctx, DLRA_ERR_ARG, "mixture weights must be finite and >= 0");
+  dlra_status s = ctx->fp64 ? set_materials_t<double>(ctx, w_host) : set_materials_t<float>(ctx, w_host);
+  if (s == DLRA_OK) ctx->materials_set = true;
+  return s;
+}
+
+dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (!beam || !beam_id) return fail(ctx, DLRA_ERR_ARG, "null beam or beam_id");
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "dlra_set_materials must precede dlra_add_beam");
+  if (ctx->step > 0) return fail(ctx, DLRA_ERR_STATE, "beams must be added before the first step");
+  if (!(beam->weight >= 0) || !(beam->spot_sigma >= 0) || !(beam->energy_sigma >= 0))
+    return fail(ctx, DLRA_ERR_ARG, "beam weight and sigmas must be >= 0");
+  return ctx->fp64 ? add_beam_t<double>(ctx, beam, beam_id) : add_beam_t<float>(ctx, beam, beam_id);
+}
+
+dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (n_steps < 0) return fail(ctx, DLRA_ERR_ARG, "n_steps must be >= 0");
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "no materials");
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (nb == 0) return fail(ctx, DLRA_ERR_STATE, "no beam added");
+  if (ctx->step + n_steps > ctx->K) return fail(ctx, DLRA_ERR_STATE, "only %d energy steps remain", ctx->K - ctx->step);
+  return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
+}
+
+dlra_status dlra_dose(dlra_ctx* ctx, double* out, int32_t out_on_device, int32_t per_mass) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (!out) return fail(ctx, DLRA_ERR_ARG, "null output");
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "no materials");
+  return ctx->fp64 ? dose_t<double>(ctx, out, out_on_device, per_mass) : dose_t<float>(ctx, out, out_on_device, per_mass);
+}
+
+dlra_status dlra_query(dlra_ctx* ctx, int32_t* step, int32_t* ranks) {
+  if (!ctx) return DLRA_ERR_ARG;
+  dlra_status s = check_device_errors(ctx);
+  if (s != DLRA_OK) return s;
+  if (step) *step = ctx->step;
+  if (ranks) {
+    size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+    for (size_t b = 0; b < nb; ++b) {
+      BeamDims* dp = ctx->fp64 ? beams_of<double>(ctx)[b].dims : beams_of<float>(ctx)[b].dims;
+      BeamDims dh;
+      CK(cudaMemcpy(&dh, dp, sizeof dh, cudaMemcpyDeviceToHost));
+      ranks[b] = dh.r;
+    }
+  }
+  return DLRA_OK;
+}
+
+dlra_status dlra_rank_log(dlra_ctx* ctx, int32_t beam_id, int32_t* log) {
+  if (!ctx) return DLRA_ERR_ARG;
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (beam_id < 0 || (size_t)beam_id >= nb || !log) return fail(ctx, DLRA_ERR_ARG, "bad beam id or null log");
+  dlra_status s = check_device_errors(ctx);
+  if (s != DLRA_OK) return s;
+  int* p = ctx->fp64 ? beams_of<double>(ctx)[beam_id].rank_log : beams_of<float>(ctx)[beam_id].rank_log;
+  CK(cudaMemcpy(log, p, sizeof(int) * 2 * ctx->K, cudaMemcpyDeviceToHost));
+  return DLRA_OK;
+}
+
+dlra_status dlra_get_state(dlra_ctx* ctx, int32_t beam_id, double* X, double* S, double* W, int32_t* r) {
+  if (!ctx) return DLRA_ERR_ARG;
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (beam_id < 0 || (size_t)beam_id >= nb || !r) return fail(ctx, DLRA_ERR_ARG, "bad beam id or null r");
+  dlra_status s = check_device_errors(ctx);
+  if (s != DLRA_OK) return s;
+  return ctx->fp64 ? get_state_t<double>(ctx, beam_id, X, S, W, r) : get_state_t<float>(ctx, beam_id, X, S, W, r);
+}
+
+dlra_status dlra_set_state(dlra_ctx* ctx, int32_t beam_id, const double* X, const double* S, const double* W,
+                           int32_t r) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (beam_id < 0 || (size_t)beam_id >= nb) return fail(ctx, DLRA_ERR_ARG, "bad beam id");
+  if (r < 0 || r > ctx->cfg.rank_max || (r > 0 && (!X || !S || !W))) return fail(ctx, DLRA_ERR_ARG, "bad state");
+  return ctx->fp64 ? set_state_t<double>(ctx, beam_id, X, S, W, r) : set_state_t<float>(ctx, beam_id, X, S, W, r);
+}
+
+dlra_status dlra_get_source(dlra_ctx* ctx, int32_t beam_id, int32_t k, double* psi, double* e_u) {
+  if (!ctx) return DLRA_ERR_ARG;
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (beam_id < 0 || (size_t)beam_id >= nb || k < 0 || k >= ctx->K) return fail(ctx, DLRA_ERR_ARG, "bad beam id or bin");
+  dlra_status s = check_device_errors(ctx);
+  if (s != DLRA_OK) return s;
+  double* ps = ctx->fp64 ? beams_of<double>(ctx)[beam_id].psi : beams_of<float>(ctx)[beam_id].psi;
+  double* eu = ctx->fp64 ? beams_of<double>(ctx)[beam_id].e_u : beams_of<float>(ctx)[beam_id].e_u;
+  if (psi) CK(cudaMemcpy(psi, ps + (long long)k * ctx->n, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  if (e_u) CK(cudaMemcpy(e_u, eu, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  return DLRA_OK;
+}
+
+dlra_status dlra_get_tables(dlra_ctx* ctx, double* A, double* absA) {
+  if (!ctx) return DLRA_ERR_ARG;
+  const size_t mm = (size_t)ctx->m * ctx->m;
+  for (int d = 0; d < 3; ++d) {
+    if (A) std::memcpy(A + d * mm, ctx->ang.A[d].data(), sizeof(double) * mm);
+    if (absA) std::memcpy(absA + d * mm, ctx->ang.absA[d].data(), sizeof(double) * mm);
+  }
+  return DLRA_OK;
+}
+
+dlra_status dlra_get_substeps(dlra_ctx* ctx, int32_t* nsub) {
+  if (!ctx || !nsub) return DLRA_ERR_ARG;
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "no materials");
+  for (int k = 0; k < ctx->K; ++k) nsub[k] = ctx->nsub[k];
+  return DLRA_OK;
+}
+
+dlra_status dlra_reset(dlra_ctx* ctx, int32_t retrace) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "no materials");
+  return ctx->fp64 ? reset_t<double>(ctx, retrace) : reset_t<float>(ctx, retrace);
+}
+
+dlra_status dlra_set_profiling(dlra_ctx* ctx, int32_t enable) {
+  if (!ctx) return DLRA_ERR_ARG;
+  prof_collect(ctx);
+  ctx->profiling = enable != 0;
+  ctx->prof_ms = 0.0;
+  ctx->prof_count = 0;
+  return DLRA_OK;
+}
+
+dlra_status dlra_kernel_stats(dlra_ctx* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx || !total_ms || !launches) return DLRA_ERR_ARG;
+  prof_collect(ctx);
+  *total_ms = ctx->prof_ms;
+  *launches = ctx->prof_count;
+  return DLRA_OK;
+}
+
+int64_t dlra_launch_count(const dlra_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* dlra_last_error(const dlra_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dlra_destroy(dlra_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->beams) {
+    if (ctx->fp64) free_beams<double>(ctx);
+    else free_beams<float>(ctx);
+  }
+  delete ctx;
+}
+
+}  // extern "C"

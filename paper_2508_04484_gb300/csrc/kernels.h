@@ -1,0 +1,79 @@
+// Launch wrappers of the small dense (one thread block) kernels and the ray tracer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dlra {
+
+// Device scalars of one low-rank state.
+struct BeamDims {
+  int r;     // rank of X, S, W
+  int qx;    // new X-side directions of the last augmentation
+  int qw;    // new W-side directions of the last augmentation
+  int pad;
+};
+
+enum ErrBits { ERR_NONFINITE = 1, ERR_CHOLESKY = 2, ERR_CAPACITY = 4 };
+
+struct RankParams {
+  int mode;          // 0 fixed, 1 adaptive, 2 schedule
+  int rank;          // fixed rank
+  int rank_max;      // capacity / adaptive maximum
+  double tol;        // adaptive relative tolerance
+  double nz_tol;     // numerically zero singular values (relative to sigma_1)
+  double cluster_tol;
+  const int* schedule;  // device [K][2] or nullptr
+};
+
+// Pivoted-Cholesky orthonormalisation factor (one block). G has ld = RBa + qcap and
+// columns j < qcap holding [Xa^T R ; R^T R](:, j). C1 (RBa x qcap, ld RBa) is the
+// first-pass projection used for the scale (nullptr: scale = trace of R^T R).
+// Writes Mout ((RBa + qcap) x qcap, ld RBa + qcap) = [-C2 T ; T] and *qout.
+void launch_orth_factor(cudaStream_t st, const double* G, const double* C1, int RBa, int qcap, double drop_tol,
+                        double* Mout, int* qout, int* err);
+
+// Truncated SVD of Sh (n2 x n2, ld n2, FP64) by one-sided Jacobi in precision T;
+// writes P, Q (n2 x RB, ld n2), S (RB x RB, ld RB), dims->r, rank_log[2*step + event].
+template <typename T>
+void launch_svd_truncate(cudaStream_t st, const double* Sh, int n2, int RB, RankParams rp, int step, int event,
+                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err);
+
+// Galerkin S-step (Sec. 2.2, Eq. KLS) with RK4 in Horner form: Sh (n2 x n2) starts at
+// [[S, 0], [0, 0]] and is advanced by nsub sub-steps with beta[4*j + 0..3];
+// operator S -> sum_k Gh_k S Ph_k, Gh and Ph laid out [(k*n2 + b)*n2 + a].
+template <typename T>
+void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
+                  const double* beta, int nsub, double* Sh);
+
+// Implicit-Euler collided L-step (Sec. 3.3.3 step 1): per degree l solves
+// (I - sum_i coef[i*(N+1)+l] Mg_i) x = S W[p,:]^T for every moment p of degree l;
+// writes L1T (m x RB, ld m) in precision T. Mg_i at [(i*RB + b)*RB + a].
+template <typename T>
+void launch_scatter_solve(cudaStream_t st, const double* Mg, int M, const double* coef, int N, const double* S,
+                          const T* W, int m, int RB, T* L1T, int* err);
+
+// Householder QR of L1T (m x r): L1T = Wt R; writes Wt (m x RB, zero beyond r) and S = R^T.
+template <typename T>
+void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S);
+
+// W-side augmentation (one block): Wh = [W | orth((I - W W^T) K)], K m x qcap of type KT,
+// rank-revealing with pivoted Gram-Schmidt (drop below drop_tol ||K||_F); writes dims->qw.
+template <typename T, typename KT>
+void launch_waug(cudaStream_t st, const T* W, int m, int RB, const KT* K, long long ldk, int qcap, double drop_tol,
+                 T* Wh, BeamDims* dims);
+
+// Source S assembly: Sh (n2 x n2) = [[S, 0], [0, 0]] + h XA (B^T Wh), XA (n2 x M, ld n2),
+// B (m x M, ld m, FP64), Wh (m x n2).
+template <typename T>
+void launch_src_assemble(cudaStream_t st, const double* S, int RB, const double* XA, const double* B, const T* Wh,
+                         int m, int M, int n2, double h, double* Sh);
+
+// CSDA ray tracer (Sec. 3.2): rays [nray][8] = (ox, oy, oz, vx, vy, vz, E0, weight).
+struct RayGeo {
+  int nx, ny, nz, two_d, K;
+  double dx, dy, dz, e_max, h, e_min, p, alpha, klam, volume;
+};
+void launch_raytrace(cudaStream_t st, const double* rays, int nray, RayGeo g, const double* f_cell,
+                     const double* tau_cell, double* psi, double* e_u);
+
+}  // namespace dlra

@@ -1,0 +1,712 @@
+// Small dense kernels of the low-rank step (one thread block each): the factors
+// of the basis augmentation, the truncation SVD, the Galerkin S-step, the implicit
+// collided L-step and its QR, the W-side augmentation and the source S assembly.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kernels.h"
+
+namespace dlra {
+
+namespace {
+
+template <typename T>
+__device__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; sbuf holds >= 32 elements. All threads get the result.
+template <typename T>
+__device__ T block_sum(T v, T* sbuf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sbuf[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sbuf[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sbuf[0] = t;
+  __syncthreads();
+  T r = sbuf[0];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// pivoted-Cholesky factor of the projected Gram (CholeskyQR with pivoting)
+// ---------------------------------------------------------------------------
+__global__ void orth_factor_kernel(const double* __restrict__ G, const double* __restrict__ C1, int RBa, int qcap,
+                                   double drop_tol, double* __restrict__ Mout, int* qout, int* err) {
+  extern __shared__ double sh[];
+  __shared__ double red[32];
+  __shared__ int s_piv, s_stop;
+  const int ldg = RBa + qcap;
+  double* A = sh;                        // qcap x qcap, col-major A[j*qcap + i]
+  double* Li = A + qcap * qcap;          // inverse of the lower factor
+  int* perm = reinterpret_cast<int*>(Li + qcap * qcap);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // G' = R^T R - C2^T C2 (C2 = Xa^T R is the top block)
+  for (int e = tid; e < qcap * qcap; e += nt) {
+    int i = e % qcap, j = e / qcap;
+    double v = G[(long long)j * ldg + RBa + i];
+    for (int a = 0; a < RBa; ++a) v -= G[(long long)i * ldg + a] * G[(long long)j * ldg + a];
+    A[e] = v;
+  }
+  for (int i = tid; i < qcap; i += nt) perm[i] = i;
+  double part = 0.0;
+  for (int i = tid; i < qcap; i += nt) part += G[(long long)i * ldg + RBa + i];
+  if (C1)
+    for (int e = tid; e < RBa * qcap; e += nt) part += C1[e] * C1[e];
+  const double scale2 = block_sum(part, red);
+  const double thr = drop_tol * drop_tol * scale2;
+  if (tid == 0) s_stop = qcap;
+  __syncthreads();
+  for (int j = 0; j < qcap; ++j) {
+    if (tid == 0) {
+      int p = j;
+      double best = A[j * qcap + j];
+      for (int i = j + 1; i < qcap; ++i)
+        if (A[i * qcap + i] > best) { best = A[i * qcap + i]; p = i; }
+      if (!(best > thr)) {
+        s_stop = j;
+        if (best != best) atomicOr(err, ERR_NONFINITE);
+      }
+      s_piv = p;
+    }
+    __syncthreads();
+    if (s_stop == j) break;
+    const int p = s_piv;
+    if (p != j) {
+      for (int k = tid; k < qcap; k += nt) {  // swap rows j, p
+        double t = A[k * qcap + j];
+        A[k * qcap + j] = A[k * qcap + p];
+        A[k * qcap + p] = t;
+      }
+      __syncthreads();
+      for (int k = tid; k < qcap; k += nt) {  // swap columns j, p
+        double t = A[j * qcap + k];
+        A[j * qcap + k] = A[p * qcap + k];
+        A[p * qcap + k] = t;
+      }
+      if (tid == 0) {
+        int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) A[j * qcap + j] = sqrt(A[j * qcap + j]);
+    __syncthreads();
+    const double djj = A[j * qcap + j];
+    for (int i = j + 1 + tid; i < qcap; i += nt) A[j * qcap + i] /= djj;
+    __syncthreads();
+    for (int e = tid; e < (qcap - j - 1) * (qcap - j - 1); e += nt) {
+      int i = j + 1 + e % (qcap - j - 1), k = j + 1 + e / (qcap - j - 1);
+      A[k * qcap + i] -= A[j * qcap + i] * A[j * qcap + k];
+    }
+    __syncthreads();
+  }
+  const int q = s_stop;
+  // inverse of the lower factor L (q x q): column c solves L x = e_c
+  for (int c = tid; c < q; c += nt) {
+    for (int i = 0; i < q; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= A[k * qcap + i] * Li[c * qcap + k];
+      Li[c * qcap + i] = (i < c) ? 0.0 : v / A[i * qcap + i];
+    }
+  }
+  __syncthreads();
+  // T[perm[i]][c] = (L^-T)[i][c] = (L^-1)[c][i] = Li[i * qcap + c] for i < q: Mout = [-C2 T ; T]
+  const int ldm = RBa + qcap;
+  for (int e = tid; e < ldm * qcap; e += nt) {
+    int row = e % ldm, c = e / ldm;
+    double v = 0.0;
+    if (c < q) {
+      if (row >= RBa) {
+        int jj = row - RBa;  // original index
+        for (int i = 0; i < q; ++i)
+          if (perm[i] == jj) { v = Li[i * qcap + c]; break; }
+      } else {
+        for (int i = 0; i < q; ++i) v -= G[(long long)perm[i] * ldg + row] * Li[i * qcap + c];
+      }
+    }
+    Mout[(long long)c * ldm + row] = v;
+  }
+  if (tid == 0) *qout = q;
+}
+
+void launch_orth_factor(cudaStream_t st, const double* G, const double* C1, int RBa, int qcap, double drop_tol,
+                        double* Mout, int* qout, int* err) {
+  size_t smem = (size_t)2 * qcap * qcap * sizeof(double) + (size_t)qcap * sizeof(int) + 16;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(orth_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  orth_factor_kernel<<<1, 256, smem, st>>>(G, C1, RBa, qcap, drop_tol, Mout, qout, err);
+}
+
+// ---------------------------------------------------------------------------
+// truncated SVD by one-sided (Hestenes) Jacobi with a round-robin ordering
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rr_pair(int round, int i, int n, int& a, int& b) {
+  if (i == 0) a = 0;
+  else a = ((i + round - 1) % (n - 1)) + 1;
+  b = ((n - 1 - i + round - 1) % (n - 1)) + 1;
+}
+
+template <typename T>
+__global__ void svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
+                                 double* __restrict__ P, double* __restrict__ Q, double* __restrict__ S,
+                                 BeamDims* dims, int* rank_log, int* err) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* A = reinterpret_cast<T*>(raw);
+  T* V = A + n2 * n2;
+  __shared__ double sig[128];
+  __shared__ int order[128];
+  __shared__ int s_rot, s_r1;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < n2 * n2; e += nt) {
+    A[e] = T(Sh[e]);
+    V[e] = (e % n2 == e / n2) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const T eps = (sizeof(T) == 8) ? T(1e-14) : T(4e-6);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < n2 - 1; ++round) {
+      for (int pi = wid; pi < n2 / 2; pi += nw) {
+        int p, q;
+        rr_pair(round, pi, n2, p, q);
+        T* ap = A + p * n2;
+        T* aq = A + q * n2;
+        T al = 0, be = 0, ga = 0;
+        for (int i = lane; i < n2; i += 32) {
+          T x = ap[i], y = aq[i];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != T(0) && fabs((double)ga) > (double)eps * sqrt((double)al * (double)be)) {
+          T zeta = (be - al) / (T(2) * ga);
+          T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          T c = T(1) / sqrt(T(1) + t * t), s = c * t;
+          for (int i = lane; i < n2; i += 32) {
+            T x = ap[i], y = aq[i];
+            ap[i] = c * x - s * y;
+            aq[i] = s * x + c * y;
+          }
+          T* vp = V + p * n2;
+          T* vq = V + q * n2;
+          for (int i = lane; i < n2; i += 32) {
+            T x = vp[i], y = vq[i];
+            vp[i] = c * x - s * y;
+            vq[i] = s * x + c * y;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!s_rot) break;
+    __syncthreads();
+  }
+  for (int j = wid; j < n2; j += nw) {
+    T s2 = 0;
+    for (int i = lane; i < n2; i += 32) s2 += A[j * n2 + i] * A[j * n2 + i];
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[j] = sqrt((double)s2);
+  }
+  __syncthreads();
+  for (int j = tid; j < n2; j += nt) {
+    int rk = 0;
+    double sj = sig[j];
+    for (int i = 0; i < n2; ++i) {
+      double si = sig[i];
+      if (si > sj || (si == sj && i < j)) ++rk;
+    }
+    order[rk] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double s1 = sig[order[0]];
+    int r1 = 0;
+    bool bad = !(s1 == s1) || isinf(s1);
+    if (bad) atomicOr(err, ERR_NONFINITE);
+    if (!bad && s1 > 0.0) {
+      int nz = 0;
+      for (int i = 0; i < n2; ++i)
+        if (sig[order[i]] > rp.nz_tol * s1) ++nz;
+      if (rp.mode == 2) {
+        r1 = rp.schedule ? rp.schedule[2 * step + event] : 0;
+        if (r1 < 0) r1 = 0;
+        if (r1 > n2) r1 = n2;
+      } else {
+        if (rp.mode == 0) {
+          r1 = rp.rank < nz ? rp.rank : nz;
+        } else {
+          double tot = 0.0;
+          for (int i = 0; i < n2; ++i) tot += sig[i] * sig[i];
+          double thr = rp.tol * sqrt(tot);
+          double tail = 0.0;
+          r1 = n2;
+          for (int r = n2; r >= 0; --r) {  // tail(r) = sum_{i >= r} sigma_i
+            if (r < n2) tail += sig[order[r]];
+            if (tail <= thr) r1 = r;
+            else break;
+          }
+          if (r1 < 1) r1 = 1;
+          if (r1 > rp.rank_max) r1 = rp.rank_max;
+          if (r1 > nz) r1 = nz;
+        }
+        int r0 = r1;
+        while (r1 > 0 && r1 < n2 && sig[order[r1 - 1]] - sig[order[r1]] <= rp.cluster_tol * s1) --r1;
+        if (r1 == 0) {
+          r1 = r0;
+          while (r1 < n2 && r1 > 0 && sig[order[r1 - 1]] - sig[order[r1]] <= rp.cluster_tol * s1) ++r1;
+        }
+      }
+      if (r1 > RB) {
+        r1 = RB;
+        atomicOr(err, ERR_CAPACITY);
+      }
+    }
+    s_r1 = r1;
+    dims->r = r1;
+    if (rank_log) rank_log[2 * step + event] = r1;
+  }
+  __syncthreads();
+  const int r1 = s_r1;
+  for (int e = tid; e < n2 * RB; e += nt) {
+    int i = e % n2, c = e / n2;
+    double pv = 0.0, qv = 0.0;
+    if (c < r1) {
+      int j = order[c];
+      double sj = sig[j];
+      pv = sj > 0.0 ? (double)A[j * n2 + i] / sj : 0.0;
+      qv = (double)V[j * n2 + i];
+    }
+    P[(long long)c * n2 + i] = pv;
+    Q[(long long)c * n2 + i] = qv;
+  }
+  for (int e = tid; e < RB * RB; e += nt) {
+    int a = e % RB, c = e / RB;
+    S[e] = (a == c && c < r1) ? sig[order[c]] : 0.0;
+  }
+}
+
+template <typename T>
+void launch_svd_truncate(cudaStream_t st, const double* Sh, int n2, int RB, RankParams rp, int step, int event,
+                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err) {
+  size_t smem = (size_t)2 * n2 * n2 * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(svd_trunc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  svd_trunc_kernel<T><<<1, 512, smem, st>>>(Sh, n2, RB, rp, step, event, P, Q, S, dims, rank_log, err);
+}
+template void launch_svd_truncate<float>(cudaStream_t, const double*, int, int, RankParams, int, int, double*, double*,
+                                         double*, BeamDims*, int*, int*);
+template void launch_svd_truncate<double>(cudaStream_t, const double*, int, int, RankParams, int, int, double*,
+                                          double*, double*, BeamDims*, int*, int*);
+
+// ---------------------------------------------------------------------------
+// Galerkin S-step with RK4 in Horner form
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void sstep_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph, int nk,
+                             const double* __restrict__ S, int RB, int n2, const double* __restrict__ beta, int nsub,
+                             double* __restrict__ Sh) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* z = reinterpret_cast<T*>(raw);
+  T* tmp = z + n2 * n2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ne = n2 * n2;
+  constexpr int EPT = 16;
+  for (int e = tid; e < ne; e += nt) {
+    int a = e % n2, c = e / n2;
+    double y = (a < RB && c < RB) ? S[c * RB + a] : 0.0;
+    Sh[e] = y;
+    z[e] = T(y);
+  }
+  __syncthreads();
+  for (int j = 0; j < nsub; ++j) {
+    for (int s = 0; s < 4; ++s) {
+      const double b = beta[4 * j + s];
+      T acc[EPT];
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) acc[i] = T(0);
+      for (int k = 0; k < nk; ++k) {
+        const double* Pk = Ph + (long long)k * n2 * n2;
+        const double* Gk = Gh + (long long)k * n2 * n2;
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          int e = tid + i * nt;
+          if (e < ne) {
+            int a = e % n2, c = e / n2;
+            T t = 0;
+            for (int q = 0; q < n2; ++q) t += z[q * n2 + a] * T(Pk[c * n2 + q]);
+            tmp[e] = t;
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          int e = tid + i * nt;
+          if (e < ne) {
+            int a = e % n2, c = e / n2;
+            T t = 0;
+            for (int q = 0; q < n2; ++q) t += T(Gk[q * n2 + a]) * tmp[c * n2 + q];
+            acc[i] += t;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        int e = tid + i * nt;
+        if (e < ne) {
+          double nv = Sh[e] + b * (double)acc[i];
+          if (s == 3) Sh[e] = nv;
+          z[e] = T(nv);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
+                  const double* beta, int nsub, double* Sh) {
+  size_t smem = (size_t)2 * n2 * n2 * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(sstep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  sstep_kernel<T><<<1, 1024, smem, st>>>(Gh, Ph, nk, S, RB, n2, beta, nsub, Sh);
+}
+template void launch_sstep<float>(cudaStream_t, const double*, const double*, int, const double*, int, int,
+                                  const double*, int, double*);
+template void launch_sstep<double>(cudaStream_t, const double*, const double*, int, const double*, int, int,
+                                   const double*, int, double*);
+
+// ---------------------------------------------------------------------------
+// implicit-Euler collided L-step: one block per degree l
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void scatter_solve_kernel(const double* __restrict__ Mg, int M, const double* __restrict__ coef, int N,
+                                     const double* __restrict__ S, const T* __restrict__ W, int m, int RB,
+                                     T* __restrict__ L1T, int* err) {
+  extern __shared__ double sh[];
+  const int l = blockIdx.x;
+  const int nr = 2 * l + 1, p0 = l * l;
+  double* A = sh;              // RB x RB, col-major
+  double* X = A + RB * RB;     // RB x nr right-hand sides / solutions
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < RB * RB; e += nt) {
+    int a = e % RB, b = e / RB;
+    double v = (a == b) ? 1.0 : 0.0;
+    for (int i = 0; i < M; ++i) v -= coef[i * (N + 1) + l] * Mg[((long long)i * RB + b) * RB + a];
+    A[e] = v;
+  }
+  for (int e = tid; e < RB * nr; e += nt) {
+    int a = e % RB, pp = e / RB;
+    double v = 0.0;
+    for (int j = 0; j < RB; ++j) v += S[j * RB + a] * (double)W[(long long)j * m + p0 + pp];
+    X[e] = v;
+  }
+  __syncthreads();
+  // Cholesky A = L L^T (lower part)
+  for (int j = 0; j < RB; ++j) {
+    if (tid == 0) {
+      double d = A[j * RB + j];
+      if (!(d > 0.0)) {
+        atomicOr(err, ERR_CHOLESKY);
+        d = 1.0;
+      }
+      A[j * RB + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double djj = A[j * RB + j];
+    for (int i = j + 1 + tid; i < RB; i += nt) A[j * RB + i] /= djj;
+    __syncthreads();
+    const int w = RB - j - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      int i = j + 1 + e % w, k = j + 1 + e / w;
+      if (k <= i) A[k * RB + i] -= A[j * RB + i] * A[j * RB + k];
+    }
+    __syncthreads();
+  }
+  // forward substitution L y = x, all right-hand sides at once
+  for (int j = 0; j < RB; ++j) {
+    for (int pp = tid; pp < nr; pp += nt) X[pp * RB + j] /= A[j * RB + j];
+    __syncthreads();
+    for (int e = tid; e < (RB - j - 1) * nr; e += nt) {
+      int i = j + 1 + e % (RB - j - 1), pp = e / (RB - j - 1);
+      X[pp * RB + i] -= A[j * RB + i] * X[pp * RB + j];
+    }
+    __syncthreads();
+  }
+  // backward substitution L^T x = y
+  for (int j = RB - 1; j >= 0; --j) {
+    for (int pp = tid; pp < nr; pp += nt) X[pp * RB + j] /= A[j * RB + j];
+    __syncthreads();
+    for (int e = tid; e < j * nr; e += nt) {
+      int i = e % j, pp = e / j;
+      X[pp * RB + i] -= A[i * RB + j] * X[pp * RB + j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < RB * nr; e += nt) {
+    int a = e % RB, pp = e / RB;
+    L1T[(long long)a * m + p0 + pp] = T(X[e]);
+  }
+}
+
+template <typename T>
+void launch_scatter_solve(cudaStream_t st, const double* Mg, int M, const double* coef, int N, const double* S,
+                          const T* W, int m, int RB, T* L1T, int* err) {
+  size_t smem = (size_t)(RB * RB + RB * (2 * N + 1)) * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(scatter_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  scatter_solve_kernel<T><<<N + 1, 256, smem, st>>>(Mg, M, coef, N, S, W, m, RB, L1T, err);
+}
+template void launch_scatter_solve<float>(cudaStream_t, const double*, int, const double*, int, const double*,
+                                          const float*, int, int, float*, int*);
+template void launch_scatter_solve<double>(cudaStream_t, const double*, int, const double*, int, const double*,
+                                           const double*, int, int, double*, int*);
+
+// ---------------------------------------------------------------------------
+// Householder QR of L1T (m x r): L1T = Wt R, S = R^T
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void qr_lt_kernel(const T* __restrict__ L1T, int m, int RB, const BeamDims* __restrict__ dims,
+                             T* __restrict__ Wt, double* __restrict__ S) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* A = reinterpret_cast<T*>(raw);   // m x RB col-major; reflectors below the diagonal
+  __shared__ T red[32];
+  __shared__ T rdiag[64], v0s[64], vn2[64];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  int r = dims->r;
+  if (r > RB) r = RB;
+  if (r > m) r = m;
+  for (int e = tid; e < m * RB; e += nt) A[e] = L1T[e];
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    T part = 0;
+    for (int i = j + tid; i < m; i += nt) part += A[j * m + i] * A[j * m + i];
+    T nrm2 = block_sum(part, red);
+    T x0 = A[j * m + j];
+    T nrm = sqrt(nrm2);
+    T alpha = (x0 >= T(0)) ? -nrm : nrm;
+    T v0 = x0 - alpha;
+    T vnorm2 = nrm2 - x0 * x0 + v0 * v0;
+    __syncthreads();
+    if (tid == 0) {
+      rdiag[j] = (nrm2 > T(0)) ? alpha : T(0);
+      v0s[j] = v0;
+      vn2[j] = (nrm2 > T(0)) ? vnorm2 : T(0);
+      A[j * m + j] = v0;  // reflector v = (v0, A[j+1:, j])
+    }
+    __syncthreads();
+    if (vn2[j] > T(0)) {
+      for (int c = j + 1 + wid; c < r; c += nw) {
+        T d = 0;
+        for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * A[c * m + i];
+        d = warp_sum(d);
+        T f = T(2) * d / vn2[j];
+        for (int i = j + lane; i < m; i += 32) A[c * m + i] -= f * A[j * m + i];
+      }
+    }
+    __syncthreads();
+  }
+  // S = R^T: R[j][j] = rdiag[j], R[j][c] = A[c*m + j] for c > j
+  for (int e = tid; e < RB * RB; e += nt) {
+    int a = e % RB, c = e / RB;  // S[a][c] = R[c][a]
+    double v = 0.0;
+    if (a < r && c < r) {
+      if (a == c) v = (double)rdiag[c];
+      else if (a > c) v = (double)A[a * m + c];
+    }
+    S[e] = v;
+  }
+  __syncthreads();
+  // Q = H_0 ... H_{r-1} applied to the first r identity columns; build in place
+  // using a second buffer region: reuse Wt (global) as workspace
+  for (int e = tid; e < m * RB; e += nt) {
+    int i = e % m, c = e / m;
+    Wt[e] = (c < r && i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {
+    if (!(vn2[j] > T(0))) continue;
+    for (int c = j + wid; c < r; c += nw) {
+      T d = 0;
+      for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * Wt[(long long)c * m + i];
+      d = warp_sum(d);
+      T f = T(2) * d / vn2[j];
+      for (int i = j + lane; i < m; i += 32) Wt[(long long)c * m + i] -= f * A[j * m + i];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S) {
+  size_t smem = (size_t)m * RB * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(qr_lt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  qr_lt_kernel<T><<<1, 512, smem, st>>>(L1T, m, RB, dims, Wt, S);
+}
+template void launch_qr_lt<float>(cudaStream_t, const float*, int, int, const BeamDims*, float*, double*);
+template void launch_qr_lt<double>(cudaStream_t, const double*, int, int, const BeamDims*, double*, double*);
+
+// ---------------------------------------------------------------------------
+// W-side augmentation: pivoted Gram-Schmidt with re-orthogonalisation
+// ---------------------------------------------------------------------------
+template <typename T, typename KT>
+__global__ void waug_kernel(const T* __restrict__ W, int m, int RB, const KT* __restrict__ K, long long ldk, int qcap,
+                            double drop_tol, T* __restrict__ Wh, BeamDims* dims) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* R = reinterpret_cast<T*>(raw);   // m x qcap
+  T* U = Wh + (long long)RB * m;      // accepted new directions, written in place
+  __shared__ T red[32];
+  __shared__ T cn[64];
+  __shared__ int used[64];
+  __shared__ int s_best;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int r = dims->r < RB ? dims->r : RB;
+  for (int e = tid; e < m * 2 * RB; e += nt) {
+    int i = e % m, c = e / m;
+    Wh[e] = (c < RB) ? W[(long long)c * m + i] : T(0);
+  }
+  T part = 0;
+  for (int e = tid; e < m * qcap; e += nt) {
+    int i = e % m, c = e / m;
+    T v = T(K[(long long)c * ldk + i]);
+    R[e] = v;
+    part += v * v;
+  }
+  for (int c = tid; c < qcap; c += nt) used[c] = 0;
+  const T scale2 = block_sum(part, red);
+  const T thr = T(drop_tol * drop_tol) * scale2;
+  // two passes of R -= W (W^T R)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c = wid; c < qcap; c += nw) {
+      for (int a = 0; a < r; ++a) {
+        T d = 0;
+        for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * R[c * m + i];
+        d = warp_sum(d);
+        for (int i = lane; i < m; i += 32) R[c * m + i] -= d * W[(long long)a * m + i];
+      }
+    }
+    __syncthreads();
+  }
+  int q = 0;
+  for (int it = 0; it < qcap; ++it) {
+    for (int c = wid; c < qcap; c += nw) {
+      T d = 0;
+      for (int i = lane; i < m; i += 32) d += R[c * m + i] * R[c * m + i];
+      d = warp_sum(d);
+      if (lane == 0) cn[c] = used[c] ? T(-1) : d;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int b = -1;
+      T bv = thr;
+      for (int c = 0; c < qcap; ++c)
+        if (cn[c] > bv) { bv = cn[c]; b = c; }
+      s_best = b;
+      if (b >= 0) used[b] = 1;
+    }
+    __syncthreads();
+    const int b = s_best;
+    if (b < 0) break;
+    // u = R[:, b] re-orthogonalised against W and the accepted directions, normalised
+    T* u = U + q * m;
+    for (int i = tid; i < m; i += nt) u[i] = R[b * m + i];
+    __syncthreads();
+    if (wid == 0) {
+      for (int a = 0; a < r; ++a) {
+        T d = 0;
+        for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * u[i];
+        d = warp_sum(d);
+        for (int i = lane; i < m; i += 32) u[i] -= d * W[(long long)a * m + i];
+      }
+      for (int a = 0; a < q; ++a) {
+        T d = 0;
+        for (int i = lane; i < m; i += 32) d += U[a * m + i] * u[i];
+        d = warp_sum(d);
+        for (int i = lane; i < m; i += 32) u[i] -= d * U[a * m + i];
+      }
+      T n2 = 0;
+      for (int i = lane; i < m; i += 32) n2 += u[i] * u[i];
+      n2 = warp_sum(n2);
+      T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
+      for (int i = lane; i < m; i += 32) u[i] *= inv;
+    }
+    __syncthreads();
+    // remove u from the remaining columns
+    for (int c = wid; c < qcap; c += nw) {
+      if (used[c]) continue;
+      T d = 0;
+      for (int i = lane; i < m; i += 32) d += u[i] * R[c * m + i];
+      d = warp_sum(d);
+      for (int i = lane; i < m; i += 32) R[c * m + i] -= d * u[i];
+    }
+    ++q;
+    __syncthreads();
+  }
+  if (tid == 0) dims->qw = q;
+}
+
+template <typename T, typename KT>
+void launch_waug(cudaStream_t st, const T* W, int m, int RB, const KT* K, long long ldk, int qcap, double drop_tol,
+                 T* Wh, BeamDims* dims) {
+  size_t smem = (size_t)m * qcap * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(waug_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  waug_kernel<T, KT><<<1, 512, smem, st>>>(W, m, RB, K, ldk, qcap, drop_tol, Wh, dims);
+}
+template void launch_waug<float, float>(cudaStream_t, const float*, int, int, const float*, long long, int, double,
+                                        float*, BeamDims*);
+template void launch_waug<float, double>(cudaStream_t, const float*, int, int, const double*, long long, int, double,
+                                         float*, BeamDims*);
+template void launch_waug<double, double>(cudaStream_t, const double*, int, int, const double*, long long, int,
+                                          double, double*, BeamDims*);
+
+// ---------------------------------------------------------------------------
+// source S assembly
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void src_assemble_kernel(const double* __restrict__ S, int RB, const double* __restrict__ XA,
+                                    const double* __restrict__ B, const T* __restrict__ Wh, int m, int M, int n2,
+                                    double h, double* __restrict__ Sh) {
+  extern __shared__ double bw[];  // M x n2: (B^T Wh)[i][c]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < M * n2; e += nt) {
+    int i = e % M, c = e / M;
+    double v = 0.0;
+    for (int p = 0; p < m; ++p) v += B[(long long)i * m + p] * (double)Wh[(long long)c * m + p];
+    bw[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < n2 * n2; e += nt) {
+    int a = e % n2, c = e / n2;
+    double v = (a < RB && c < RB) ? S[c * RB + a] : 0.0;
+    for (int i = 0; i < M; ++i) v += h * XA[(long long)i * n2 + a] * bw[c * M + i];
+    Sh[e] = v;
+  }
+}
+
+template <typename T>
+void launch_src_assemble(cudaStream_t st, const double* S, int RB, const double* XA, const double* B, const T* Wh,
+                         int m, int M, int n2, double h, double* Sh) {
+  size_t smem = (size_t)M * n2 * sizeof(double);
+  src_assemble_kernel<T><<<1, 512, smem, st>>>(S, RB, XA, B, Wh, m, M, n2, h, Sh);
+}
+template void launch_src_assemble<float>(cudaStream_t, const double*, int, const double*, const double*, const float*,
+                                         int, int, int, double, double*);
+template void launch_src_assemble<double>(cudaStream_t, const double*, int, const double*, const double*,
+                                          const double*, int, int, int, double, double*);
+
+}  // namespace dlra

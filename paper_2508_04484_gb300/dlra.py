@@ -1,0 +1,383 @@
+"""Thin Python binding of the C ABI in ``include/dlra.h``.
+
+Argument marshalling only: every computation runs in the CUDA library
+``libdlra.so``. The functions carry the C names; ``Solver`` bundles them for one
+context. Device buffers may be given as PyTorch CUDA tensors (their data pointer
+is passed with the matching ``*_on_device`` flag); the CUDA stream of a context
+is a borrowed ``cudaStream_t`` (e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdlra.so")
+
+DLRA_OK = 0
+STATUS = {0: "DLRA_OK", 1: "DLRA_ERR_ARG", 2: "DLRA_ERR_STATE", 3: "DLRA_ERR_CUDA", 4: "DLRA_ERR_OOM",
+          5: "DLRA_ERR_NONFINITE", 6: "DLRA_ERR_RANK", 7: "DLRA_ERR_TIMEOUT"}
+FOKKER_PLANCK, BOLTZMANN = 0, 1
+RANK_FIXED, RANK_ADAPTIVE, RANK_SCHEDULE = 0, 1, 2
+FP64, FP32_MIXED = 0, 1
+
+
+class DlraError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dlra_config(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("sh_degree", C.c_int32), ("collision", C.c_int32), ("transport_correction", C.c_int32),
+                ("rank_mode", C.c_int32), ("rank", C.c_int32), ("rank_max", C.c_int32),
+                ("trunc_tol", C.c_double), ("rank_schedule", C.POINTER(C.c_int32)),
+                ("e_max", C.c_double), ("e_min", C.c_double), ("n_energy_steps", C.c_int32),
+                ("cfl_max", C.c_double), ("precision", C.c_int32),
+                ("bk_p", C.c_double), ("bk_alpha", C.c_double), ("t100", C.c_double),
+                ("cuda_stream", C.c_void_p)]
+
+
+class dlra_material(C.Structure):
+    _fields_ = [("density", C.c_double), ("sp_ratio", C.c_double), ("scatter_ratio", C.c_double),
+                ("screening", C.c_double)]
+
+
+class dlra_beam(C.Structure):
+    _fields_ = [("energy", C.c_double), ("energy_sigma", C.c_double), ("pos", C.c_double * 3),
+                ("dir", C.c_double * 3), ("spot_sigma", C.c_double), ("weight", C.c_double)]
+
+
+# names, argument types and return type of every entry point of include/dlra.h
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int32)
+SIGNATURES = {
+    "dlra_init": ([C.POINTER(dlra_config), C.POINTER(_P)], C.c_int),
+    "dlra_set_materials": ([_P, C.c_int32, C.POINTER(dlra_material), _P, C.c_int32], C.c_int),
+    "dlra_add_beam": ([_P, C.POINTER(dlra_beam), _IP], C.c_int),
+    "dlra_step": ([_P, C.c_int32], C.c_int),
+    "dlra_dose": ([_P, _P, C.c_int32, C.c_int32], C.c_int),
+    "dlra_query": ([_P, _IP, _IP], C.c_int),
+    "dlra_rank_log": ([_P, C.c_int32, _IP], C.c_int),
+    "dlra_get_state": ([_P, C.c_int32, _DP, _DP, _DP, _IP], C.c_int),
+    "dlra_set_state": ([_P, C.c_int32, _DP, _DP, _DP, C.c_int32], C.c_int),
+    "dlra_get_source": ([_P, C.c_int32, C.c_int32, _DP, _DP], C.c_int),
+    "dlra_get_tables": ([_P, _DP, _DP], C.c_int),
+    "dlra_get_substeps": ([_P, _IP], C.c_int),
+    "dlra_reset": ([_P, C.c_int32], C.c_int),
+    "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
+    "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
+    "dlra_launch_count": ([_P], C.c_int64),
+    "dlra_last_error": ([_P], C.c_char_p),
+    "dlra_destroy": ([_P], None),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdlra.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2508_04484_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status):
+    if status != DLRA_OK:
+        msg = load().dlra_last_error(ctx)
+        raise DlraError(status, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_IP)
+
+
+def make_config(cfg: dict, stream=None):
+    c = dlra_config()
+    c.nx, c.ny, c.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg["nz"])
+    c.dx, c.dy, c.dz = float(cfg["dx"]), float(cfg["dy"]), float(cfg["dz"])
+    c.sh_degree = int(cfg["N"])
+    coll = cfg["collision"]
+    if isinstance(coll, str):
+        coll = BOLTZMANN if coll.lower().startswith("b") else FOKKER_PLANCK
+    c.collision = int(coll)
+    c.transport_correction = int(cfg.get("transport_correction", 1))
+    c.rank_mode = int(cfg.get("rank_mode", RANK_FIXED))
+    c.rank = int(cfg.get("rank", 5))
+    c.rank_max = int(cfg.get("rank_max", max(c.rank, 1)))
+    c.trunc_tol = float(cfg.get("trunc_tol", 1e-3))
+    c.e_max, c.e_min = float(cfg["e_max"]), float(cfg["e_min"])
+    c.n_energy_steps = int(cfg["n_steps"])
+    c.cfl_max = float(cfg.get("cfl", 0.6))
+    c.precision = int(cfg.get("precision", FP64))
+    c.bk_p = float(cfg.get("bk_p", 1.77))
+    c.bk_alpha = float(cfg.get("bk_alpha", 0.0022))
+    c.t100 = float(cfg.get("t100", 1.72e-4))
+    c.cuda_stream = stream
+    sched = cfg.get("rank_schedule")
+    keep = None
+    if sched is not None:
+        keep = np.ascontiguousarray(np.asarray(sched, dtype=np.int32).reshape(-1))
+        c.rank_schedule = _iptr(keep)
+    return c, keep
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+# ---------------------------------------------------------------------------
+def dlra_init(cfg: dict, stream=None):
+    lib = load()
+    c, keep = make_config(cfg, stream)
+    h = _P()
+    st = lib.dlra_init(C.byref(c), C.byref(h))
+    if st != DLRA_OK:
+        msg = lib.dlra_last_error(h) if h.value else b"invalid configuration"
+        if h.value:
+            lib.dlra_destroy(h)
+        raise DlraError(st, msg.decode())
+    del keep
+    return h
+
+
+def dlra_set_materials(ctx, materials, w):
+    mats = (dlra_material * len(materials))()
+    for i, m in enumerate(materials):
+        mats[i].density = m["density"]
+        mats[i].sp_ratio = m.get("sp_ratio", 1.0)
+        mats[i].scatter_ratio = m.get("scatter_ratio", 1.0)
+        mats[i].screening = m.get("screening", 1e-3)
+    if _is_cuda_tensor(w):
+        _check(ctx, load().dlra_set_materials(ctx, len(materials), mats, C.c_void_p(w.data_ptr()), 1))
+    else:
+        wa = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        _check(ctx, load().dlra_set_materials(ctx, len(materials), mats, wa.ctypes.data_as(C.c_void_p), 0))
+
+
+def dlra_add_beam(ctx, beam: dict) -> int:
+    b = dlra_beam()
+    b.energy = beam["energy"]
+    b.energy_sigma = beam.get("energy_sigma", 0.0)
+    for i in range(3):
+        b.pos[i] = beam["pos"][i]
+        b.dir[i] = beam["dir"][i]
+    b.spot_sigma = beam.get("spot_sigma", 0.0)
+    b.weight = beam.get("weight", 1.0)
+    bid = C.c_int32()
+    _check(ctx, load().dlra_add_beam(ctx, C.byref(b), C.byref(bid)))
+    return bid.value
+
+
+def dlra_step(ctx, n_steps: int):
+    _check(ctx, load().dlra_step(ctx, int(n_steps)))
+
+
+def dlra_dose(ctx, n: int = None, out=None, per_mass=False):
+    """Dose into ``out`` (torch CUDA tensor or numpy float64) or a new numpy array of length n."""
+    if out is not None and _is_cuda_tensor(out):
+        _check(ctx, load().dlra_dose(ctx, C.c_void_p(out.data_ptr()), 1, int(per_mass)))
+        return out
+    if out is None:
+        out = np.zeros(n)
+    _check(ctx, load().dlra_dose(ctx, out.ctypes.data_as(C.c_void_p), 0, int(per_mass)))
+    return out
+
+
+def dlra_query(ctx, n_beams: int = 0):
+    step = C.c_int32()
+    ranks = np.zeros(max(n_beams, 1), dtype=np.int32)
+    _check(ctx, load().dlra_query(ctx, C.byref(step), _iptr(ranks)))
+    return step.value, ranks[:n_beams]
+
+
+def dlra_rank_log(ctx, beam_id: int, K: int):
+    log = np.zeros(2 * K, dtype=np.int32)
+    _check(ctx, load().dlra_rank_log(ctx, beam_id, _iptr(log)))
+    return log.reshape(K, 2)
+
+
+def dlra_get_state(ctx, beam_id: int, n: int, m: int, rank_max: int):
+    RB = (rank_max + 3) // 4 * 4
+    X = np.zeros(n * RB)
+    S = np.zeros(RB * RB)
+    W = np.zeros(m * RB)
+    r = C.c_int32()
+    _check(ctx, load().dlra_get_state(ctx, beam_id, _dptr(X), _dptr(S), _dptr(W), C.byref(r)))
+    r = r.value
+    X = X.reshape(RB, n).T[:, :r].copy()
+    W = W.reshape(RB, m).T[:, :r].copy()
+    S = S.reshape(RB, RB).T[:r, :r].copy()
+    return X, S, W
+
+
+def dlra_set_state(ctx, beam_id: int, X, S, W, rank_max: int):
+    X = np.asarray(X, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    r = X.shape[1]
+    RB = (rank_max + 3) // 4 * 4
+    Xc = np.ascontiguousarray(X.T).reshape(-1)
+    Wc = np.ascontiguousarray(W.T).reshape(-1)
+    Sc = np.zeros((RB, RB))
+    Sc[:r, :r] = S.T
+    Sc = np.ascontiguousarray(Sc).reshape(-1)
+    _check(ctx, load().dlra_set_state(ctx, beam_id, _dptr(Xc), _dptr(Sc), _dptr(Wc), r))
+
+
+def dlra_get_source(ctx, beam_id: int, k: int, n: int):
+    psi = np.zeros(n)
+    e_u = np.zeros(n)
+    _check(ctx, load().dlra_get_source(ctx, beam_id, k, _dptr(psi), _dptr(e_u)))
+    return psi, e_u
+
+
+def dlra_get_tables(ctx, m: int):
+    A = np.zeros(3 * m * m)
+    absA = np.zeros(3 * m * m)
+    _check(ctx, load().dlra_get_tables(ctx, _dptr(A), _dptr(absA)))
+    return A.reshape(3, m, m), absA.reshape(3, m, m)
+
+
+def dlra_get_substeps(ctx, K: int):
+    out = np.zeros(K, dtype=np.int32)
+    _check(ctx, load().dlra_get_substeps(ctx, _iptr(out)))
+    return out
+
+
+def dlra_reset(ctx, retrace=True):
+    _check(ctx, load().dlra_reset(ctx, int(bool(retrace))))
+
+
+def dlra_set_profiling(ctx, enable=True):
+    _check(ctx, load().dlra_set_profiling(ctx, int(bool(enable))))
+
+
+def dlra_kernel_stats(ctx):
+    ms = C.c_double()
+    cnt = C.c_int64()
+    _check(ctx, load().dlra_kernel_stats(ctx, C.byref(ms), C.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def dlra_launch_count(ctx) -> int:
+    return int(load().dlra_launch_count(ctx))
+
+
+def dlra_last_error(ctx) -> str:
+    return load().dlra_last_error(ctx).decode()
+
+
+def dlra_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().dlra_destroy(ctx)
+
+
+def _is_cuda_tensor(x):
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+class Solver:
+    """One context: configuration dict, materials, mixture weights, beams."""
+
+    def __init__(self, cfg: dict, materials=None, w=None, beams=(), stream=None):
+        self.cfg = dict(cfg)
+        self.n = int(cfg["nx"]) * int(cfg["ny"]) * int(cfg["nz"])
+        self.m = (int(cfg["N"]) + 1) ** 2
+        self.K = int(cfg["n_steps"])
+        self.rank_max = int(cfg.get("rank_max", cfg.get("rank", 5)))
+        self.ctx = dlra_init(cfg, stream)
+        self.beam_ids = []
+        if materials is not None:
+            self.set_materials(materials, w)
+        for b in beams:
+            self.add_beam(b)
+
+    def set_materials(self, materials, w):
+        dlra_set_materials(self.ctx, materials, w)
+
+    def add_beam(self, beam):
+        self.beam_ids.append(dlra_add_beam(self.ctx, beam))
+        return self.beam_ids[-1]
+
+    def step(self, n_steps=1):
+        dlra_step(self.ctx, n_steps)
+
+    def run(self):
+        step, _ = self.query()
+        if self.K - step:
+            self.step(self.K - step)
+        return self.dose()
+
+    def dose(self, out=None, per_mass=False):
+        return dlra_dose(self.ctx, self.n, out, per_mass)
+
+    def query(self):
+        return dlra_query(self.ctx, len(self.beam_ids))
+
+    def rank_log(self, beam_id=0):
+        return dlra_rank_log(self.ctx, beam_id, self.K)
+
+    def get_state(self, beam_id=0):
+        return dlra_get_state(self.ctx, beam_id, self.n, self.m, self.rank_max)
+
+    def set_state(self, X, S, W, beam_id=0):
+        dlra_set_state(self.ctx, beam_id, X, S, W, self.rank_max)
+
+    def source(self, k, beam_id=0):
+        return dlra_get_source(self.ctx, beam_id, k, self.n)
+
+    def tables(self):
+        return dlra_get_tables(self.ctx, self.m)
+
+    def substeps(self):
+        return dlra_get_substeps(self.ctx, self.K)
+
+    def reset(self, retrace=True):
+        dlra_reset(self.ctx, retrace)
+
+    def set_profiling(self, enable=True):
+        dlra_set_profiling(self.ctx, enable)
+
+    def kernel_stats(self):
+        return dlra_kernel_stats(self.ctx)
+
+    def launch_count(self):
+        return dlra_launch_count(self.ctx)
+
+    def close(self):
+        dlra_destroy(self.ctx)
+        self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.ctx is not None:
+                self.close()
+        except Exception:
+            pass
