@@ -39,7 +39,7 @@ __device__ T block_sum(T v, T* sbuf) {
 // ---------------------------------------------------------------------------
 // pivoted-Cholesky factor of the projected Gram (CholeskyQR with pivoting)
 // ---------------------------------------------------------------------------
-__global__ void orth_factor_kernel(const double* __restrict__ G, const double* __restrict__ C1, int RBa, int qcap,
+__global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restrict__ G, const double* __restrict__ C1, int RBa, int qcap,
                                    double drop_tol, double* __restrict__ Mout, int* qout, int* err) {
   extern __shared__ double sh[];
   __shared__ double red[32];
@@ -156,7 +156,7 @@ __device__ __forceinline__ void rr_pair(int round, int i, int n, int& a, int& b)
 }
 
 template <typename T>
-__global__ void svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
+__global__ void __launch_bounds__(512) svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
                                  double* __restrict__ P, double* __restrict__ Q, double* __restrict__ S,
                                  BeamDims* dims, int* rank_log, int* err) {
   extern __shared__ __align__(16) unsigned char raw[];
@@ -316,7 +316,7 @@ template void launch_svd_truncate<double>(cudaStream_t, const double*, int, int,
 // Galerkin S-step with RK4 in Horner form
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void sstep_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph, int nk,
+__global__ void __launch_bounds__(1024) sstep_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph, int nk,
                              const double* __restrict__ S, int RB, int n2, const double* __restrict__ beta, int nsub,
                              double* __restrict__ Sh) {
   extern __shared__ __align__(16) unsigned char raw[];
@@ -394,7 +394,7 @@ template void launch_sstep<double>(cudaStream_t, const double*, const double*, i
 // implicit-Euler collided L-step: one block per degree l
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void scatter_solve_kernel(const double* __restrict__ Mg, int M, const double* __restrict__ coef, int N,
+__global__ void __launch_bounds__(256) scatter_solve_kernel(const double* __restrict__ Mg, int M, const double* __restrict__ coef, int N,
                                      const double* __restrict__ S, const T* __restrict__ W, int m, int RB,
                                      T* __restrict__ L1T, int* err) {
   extern __shared__ double sh[];
@@ -480,7 +480,7 @@ template void launch_scatter_solve<double>(cudaStream_t, const double*, int, con
 // Householder QR of L1T (m x r): L1T = Wt R, S = R^T
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void qr_lt_kernel(const T* __restrict__ L1T, int m, int RB, const BeamDims* __restrict__ dims,
+__global__ void __launch_bounds__(512) qr_lt_kernel(const T* __restrict__ L1T, int m, int RB, const BeamDims* __restrict__ dims,
                              T* __restrict__ Wt, double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char raw[];
   T* A = reinterpret_cast<T*>(raw);   // m x RB col-major; reflectors below the diagonal
@@ -564,7 +564,7 @@ template void launch_qr_lt<double>(cudaStream_t, const double*, int, int, const 
 // W-side augmentation: pivoted Gram-Schmidt with re-orthogonalisation
 // ---------------------------------------------------------------------------
 template <typename T, typename KT>
-__global__ void waug_kernel(const T* __restrict__ W, int m, int RB, const KT* __restrict__ K, long long ldk, int qcap,
+__global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int m, int RB, const KT* __restrict__ K, long long ldk, int qcap,
                             double drop_tol, T* __restrict__ Wh, BeamDims* dims) {
   extern __shared__ __align__(16) unsigned char raw[];
   T* R = reinterpret_cast<T*>(raw);   // m x qcap
@@ -678,7 +678,7 @@ template void launch_waug<double, double>(cudaStream_t, const double*, int, int,
 // source S assembly
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void src_assemble_kernel(const double* __restrict__ S, int RB, const double* __restrict__ XA,
+__global__ void __launch_bounds__(512) src_assemble_kernel(const double* __restrict__ S, int RB, const double* __restrict__ XA,
                                     const double* __restrict__ B, const T* __restrict__ Wh, int m, int M, int n2,
                                     double h, double* __restrict__ Sh) {
   extern __shared__ double bw[];  // M x n2: (B^T Wh)[i][c]
