@@ -42,6 +42,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--energy-steps", type=int, default=0,
+                   help="profiling only: stop each solve after this many energy steps")
     return p.parse_args()
 
 
@@ -198,7 +201,7 @@ def main():
     B.build()
     cfg, mats, w, beams = _workload()
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    K = cfg["n_steps"]
+    K = cfg["n_steps"] if args.energy_steps <= 0 else min(args.energy_steps, cfg["n_steps"])
     stream = torch.cuda.Stream(device=dev)
     solver = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
     nsub = solver.substeps()
@@ -213,7 +216,8 @@ def main():
     for _ in range(args.warmup):
         one_solve()
     torch.cuda.synchronize()
-    log = solver.rank_log()
+    log = solver.rank_log()[:K]
+    nsub = nsub[:K]
     r_start, updates, stage_launches = _rank_stats(log, nsub, n)
     clocks = Clocks(dev.index)
     # ---- timed region: K whole solves, L2 flushed between them ----
@@ -277,7 +281,7 @@ def main():
                 "avg_launch_us": avg_launch_ms * 1000.0}
     # ---- end to end through the public API with host buffers ----
     e2e = None
-    if rank == 0 or ws > 1:
+    if (rank == 0 or ws > 1) and not args.no_e2e:
         w_host = np.ascontiguousarray(w, dtype=np.float64)
         dose_host = np.zeros(n)
         e2e_times = []

@@ -51,16 +51,6 @@ __global__ void pstack_kernel(const double* __restrict__ P, int RB, int nk, T* _
   Pst[e] = T(P[((long long)k * RB + c) * RB + cp]);
 }
 
-__global__ void gt_kernel(const double* __restrict__ G, int RB, int nk, double* __restrict__ Gt) {
-  // Gt[(k*RB + c)*RB + a] = G_k[c][a] = G[(k*RB + a)*RB + c]
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  int tot = nk * RB * RB;
-  if (e >= tot) return;
-  int a = e % RB, j = e / RB;
-  int k = j / RB, c = j % RB;
-  Gt[e] = G[((long long)k * RB + a) * RB + c];
-}
-
 template <typename T>
 __global__ void src_vec_kernel(const T* __restrict__ w, const double* __restrict__ psi, long long n, int M,
                                T* __restrict__ A) {
@@ -133,7 +123,7 @@ void gemm(cudaStream_t st, long long rows, int N, int Q, AL al, BL bl, EP ep, in
   int BN = std::min(64, (N + 3) / 4 * 4);
   int threads = 16 * (BN / 4);
   dim3 grid((unsigned)((rows + GM_BM - 1) / GM_BM), (unsigned)((N + BN - 1) / BN));
-  size_t smem = (size_t)(BK * GM_BM + BK * BN) * sizeof(T);
+  size_t smem = (size_t)(BK * GM_BM + BK * BN) * sizeof(T) + AL::kExtra;
   gemm_kernel<T, BK, AL, BL, EP><<<grid, threads, smem, st>>>(rows, N, Q, al, bl, ep);
   ++nl;
 }
@@ -142,11 +132,17 @@ template <typename T, class F>
 void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int* adim, int acap, int ncols_j, F f,
           double* out, long long ldo, int64_t& nl) {
   if (rows <= 0 || acap <= 0 || ncols_j <= 0) return;
-  int gy = (acap + 63) / 64, gz = (ncols_j + 63) / 64;
+  const long long area64 = (long long)((acap + 63) / 64) * ((ncols_j + 63) / 64) * 4096;
+  const long long area32 = (long long)((acap + 31) / 32) * ((ncols_j + 31) / 32) * 1024;
+  const int tile = area32 < area64 ? 32 : 64;
+  int gy = (acap + tile - 1) / tile, gz = (ncols_j + tile - 1) / tile;
   long long want = (rows + GR_TC - 1) / GR_TC;
-  long long cap = std::max(1, 1216 / (gy * gz));
+  long long cap = std::max(1, (tile == 64 ? 1216 : 2432) / (gy * gz));
   int gx = (int)std::max(1LL, std::min(want, cap));
-  gram_kernel<T, F><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  if (tile == 64)
+    gram_kernel<T, F, 64><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  else
+    gram_kernel<T, F, 32><<<dim3(gx, gy, gz), 64, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
   ++nl;
 }
 
@@ -419,8 +415,6 @@ struct Engine {
     cudaMemsetAsync(ctx->G1, 0, sizeof(double) * nk * RB * RB, st);
     gram<T>(st, n, B.X, n, rdim, RB, nk * RB, FStencil<T>{B.X, n, P(ctx->inv_rho), ctx->geo, RB, rdim}, ctx->G1, RB,
             nl);
-    gt_kernel<<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->G1, RB, nk, ctx->Gt);
-    ++nl;
     // K-step: K0 = X S, RK4 Horner stages z <- y + beta L(z)
     T* y = P(ctx->Kb[0]);
     T* za = P(ctx->Kb[1]);
@@ -448,12 +442,9 @@ struct Engine {
                     BLoadRow<T, T>{P(ctx->Pst), RB, nk * RB, RB}, EpiKStage<T>{outs[s], y, n, T(beta[s])}, nl);
         prof_end(ctx);
         zin = outs[s];
-        // m-side: Z_k = z G_k^T, out = y + beta sum_k A^s_d Z_k
-        gemm<T, 16>(st, m, nk * RB, RB, ALoadPlain<T>{lin, m, rdim, RB},
-                    BLoadCol<T, double>{ctx->Gt, RB, nullptr, RB, nullptr, nk * RB},
-                    EpiStore<T>{Zm, m, nullptr, m, T(1), T(0)}, nl);
-        gemm<T, 16>(st, m, RB, nk * m, ALoadRowBlocks<T>{P(ctx->Apm), m, nk}, BLoadKBlocks<T>{Zm, m, RB, nk},
-                    EpiKStage<T>{louts[s], ly, m, T(beta[s])}, nl);
+        // m-side: out = y + beta sum_k A^s_d z G_k^T
+        lstage_kernel<T><<<m, 128, 0, st>>>(P(ctx->Apm), m, nk, lin, ly, louts[s], ctx->G1, RB, rdim, T(beta[s]));
+        ++nl;
         lin = louts[s];
       }
     }

@@ -54,6 +54,64 @@ __device__ __forceinline__ void cell_coords(long long i, const Geo& g, int& ix, 
   ix = (int)(rem - (long long)iy * g.nx);
 }
 
+// Per-tile stencil tables: for the cells row0 .. row0 + TT - 1 and the 13 stencil
+// points (0: centre; 1 + 4d .. 4 + 4d: -1, -2, +1, +2 along direction d), the linear
+// offset of the point and rho^-1 there (offset 0 and value 0 outside the grid, so
+// the ghost layers are zero without branches).
+template <typename T, int TT>
+__device__ void stencil_tables(int* sOff, T* sR, long long row0, long long rows, const T* __restrict__ inv_rho,
+                               const Geo& g) {
+  for (int e = threadIdx.x; e < 13 * TT; e += blockDim.x) {
+    const int pt = e / TT, t = e % TT;
+    const long long r = row0 + t;
+    int off = 0;
+    T val = T(0);
+    if (r < rows) {
+      const int ri = (int)r;
+      const int nxy = (int)g.nxy;
+      const int iz = ri / nxy;
+      const int rem = ri - iz * nxy;
+      const int iy = rem / g.nx;
+      const int ix = rem - iy * g.nx;
+      if (pt == 0) {
+        val = inv_rho[r];
+      } else {
+        const int d = (pt - 1) >> 2, q = (pt - 1) & 3;
+        const int delta = (q == 0) ? -1 : (q == 1) ? -2 : (q == 2) ? 1 : 2;
+        const int c = d == 0 ? ix : (d == 1 ? iy : iz);
+        const int L = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+        const int st = d == 0 ? 1 : (d == 1 ? g.nx : nxy);
+        if (c + delta >= 0 && c + delta < L) {
+          off = delta * st;
+          val = inv_rho[r + off];
+        }
+      }
+    }
+    sOff[e] = off;
+    sR[e] = val;
+  }
+}
+
+// The nk stencil values of column col at tile cell t from the tables.
+template <typename T, int TT>
+__device__ __forceinline__ void stencil_values(const T* __restrict__ col, const int* sOff, const T* sR, int t,
+                                               const Geo& g, T* out) {
+  const T v0 = col[0] * sR[t];
+#pragma unroll
+  for (int da = 0; da < 3; ++da) {
+    if (da >= g.nact) break;
+    const int d = g.dirs[da];
+    const int b = 1 + 4 * d;
+    const T inv = T(g.inv2d[d]);
+    const T vm1 = col[sOff[b * TT + t]] * sR[b * TT + t];
+    const T vm2 = col[sOff[(b + 1) * TT + t]] * sR[(b + 1) * TT + t];
+    const T vp1 = col[sOff[(b + 2) * TT + t]] * sR[(b + 2) * TT + t];
+    const T vp2 = col[sOff[(b + 3) * TT + t]] * sR[(b + 3) * TT + t];
+    out[2 * da] = (T(-3) * v0 + T(4) * vm1 - vm2) * inv;
+    out[2 * da + 1] = (T(3) * v0 - T(4) * vp1 + vp2) * inv;
+  }
+}
+
 __device__ __forceinline__ int dev_dim(const int* p, int cap) {
   if (p == nullptr) return cap;
   int v = *p;
@@ -69,11 +127,13 @@ constexpr int GM_BM = 64;
 // A producer: plain column-major tall matrix.
 template <typename T>
 struct ALoadPlain {
+  static constexpr int kExtra = 0;
   const T* A;
   long long lda;
   const int* qdim;  // actual number of columns (device), nullptr = Q
   int qcap;
-  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows) const {
+  __device__ void init(void*, long long, long long) const {}
+  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows, const void*) const {
     const int Qa = dev_dim(qdim, qcap);
     for (int e = threadIdx.x; e < BK * GM_BM; e += blockDim.x) {
       int kk = e / GM_BM, t = e % GM_BM;
@@ -85,16 +145,25 @@ struct ALoadPlain {
 };
 
 // A producer: virtual matrix of stencil values, column q = c * nk + k holds
-// D_k(rho^-1 Z[:, c]); BK must be a multiple of nk.
+// D_k(rho^-1 Z[:, c]); BK must be a multiple of nk. Neighbour offsets and rho^-1 of
+// the tile are tabulated once per block (init).
 template <typename T>
 struct ALoadStencil {
+  static constexpr int kExtra = 13 * GM_BM * (int)(sizeof(int) + sizeof(T));
   const T* Z;
   long long ldz;
   const T* inv_rho;
   Geo g;
   const int* cdim;  // actual number of input columns of Z
   int ccap;
-  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows) const {
+  __device__ void init(void* ex, long long row0, long long rows) const {
+    int* sOff = reinterpret_cast<int*>(ex);
+    T* sR = reinterpret_cast<T*>(sOff + 13 * GM_BM);
+    stencil_tables<T, GM_BM>(sOff, sR, row0, rows, inv_rho, g);
+  }
+  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows, const void* ex) const {
+    const int* sOff = reinterpret_cast<const int*>(ex);
+    const T* sR = reinterpret_cast<const T*>(sOff + 13 * GM_BM);
     const int nk = 2 * g.nact;
     const int nc = BK / nk, c0 = q0 / nk;
     const int Ca = dev_dim(cdim, ccap);
@@ -102,14 +171,14 @@ struct ALoadStencil {
       int cc = e / GM_BM, t = e % GM_BM;
       long long r = row0 + t;
       int c = c0 + cc;
+      T v[6];
       if (r < rows && c < Ca) {
-        int ix, iy, iz;
-        cell_coords(r, g, ix, iy, iz);
-        const T* col = Z + (long long)c * ldz;
-        for (int k = 0; k < nk; ++k) sA[(cc * nk + k) * GM_BM + t] = stencil_value(col, inv_rho, r, ix, iy, iz, k, g);
+        stencil_values<T, GM_BM>(Z + (long long)c * ldz + r, sOff, sR, t, g, v);
       } else {
-        for (int k = 0; k < nk; ++k) sA[(cc * nk + k) * GM_BM + t] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = T(0);
       }
+      for (int k = 0; k < nk; ++k) sA[(cc * nk + k) * GM_BM + t] = v[k];
     }
   }
 };
@@ -117,9 +186,11 @@ struct ALoadStencil {
 // A producer: nk dense row-major m x m matrices side by side, A[p][k*m + q] = M_k[p][q].
 template <typename T>
 struct ALoadRowBlocks {
+  static constexpr int kExtra = 0;
   const T* M;  // [nk][m][m]
   int m, nk;
-  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows) const {
+  __device__ void init(void*, long long, long long) const {}
+  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows, const void*) const {
     for (int e = threadIdx.x; e < BK * GM_BM; e += blockDim.x) {
       int t = e / BK, kk = e % BK;  // consecutive threads walk q (contiguous in a row)
       long long r = row0 + t;
@@ -133,10 +204,12 @@ struct ALoadRowBlocks {
 // A producer: plain row-major matrix, A(r, q) = M[r * ld + q].
 template <typename T>
 struct ALoadRowMajor {
+  static constexpr int kExtra = 0;
   const T* M;
   long long ld;
   int Q;
-  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows) const {
+  __device__ void init(void*, long long, long long) const {}
+  __device__ void load(T* sA, int BK, int q0, long long row0, long long rows, const void*) const {
     for (int e = threadIdx.x; e < BK * GM_BM; e += blockDim.x) {
       int t = e / BK, kk = e % BK;
       long long r = row0 + t;
@@ -241,17 +314,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(long long rows, int N, int Q,
   const int tnc = blockDim.x / 16;
   const int BN = tnc * 4;
   T* sB = sA + BK * GM_BM;
+  void* ex = reinterpret_cast<void*>(sB + BK * BN);
   const int tid = threadIdx.x;
   const int tm = tid % 16, tn = tid / 16;
   const long long row0 = (long long)blockIdx.x * GM_BM;
   const int c0 = blockIdx.y * BN;
+  if (AL::kExtra > 0) {
+    al.init(ex, row0, rows);
+    __syncthreads();
+  }
   T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   for (int q0 = 0; q0 < Q; q0 += BK) {
-    al.load(sA, BK, q0, row0, rows);
+    al.load(sA, BK, q0, row0, rows, ex);
     bl.load(sB, BK, BN, q0, c0);
     __syncthreads();
 #pragma unroll 4
@@ -281,22 +359,64 @@ __global__ void __launch_bounds__(256) gemm_kernel(long long rows, int N, int Q,
 }
 
 // ---------------------------------------------------------------------------
+// m-side RK4 stage of the L-step: out = y + beta * sum_k Apm_k z G_k^T
+// (Apm_k = A^s_d row-major m x m, G_k at G[(k*RB + b)*RB + a] = G_k[a][b]).
+// Each block owns LS_RPB rows: V_k = Apm_k(rows, :) z, acc += V_k G_k^T.
+// ---------------------------------------------------------------------------
+// One block per moment row p: V_k(a) = Apm_k[p, :] z(:, a) by warp dot products,
+// then out(p, c) = y(p, c) + beta sum_k sum_a V_k(a) G_k[c][a].
+template <typename T>
+__global__ void __launch_bounds__(128) lstage_kernel(const T* __restrict__ Apm, int m, int nk,
+                                                     const T* __restrict__ z, const T* __restrict__ y,
+                                                     T* __restrict__ out, const double* __restrict__ G, int RB,
+                                                     const int* __restrict__ rdim, T beta) {
+  __shared__ T sV[6 * 64];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int r = dev_dim(rdim, RB);
+  const int p = blockIdx.x;
+  for (int pr = wid; pr < nk * r; pr += nw) {
+    const int k = pr / r, a = pr - k * r;
+    const T* Ak = Apm + ((long long)k * m + p) * m;
+    const T* za = z + (long long)a * m;
+    T v = T(0);
+    for (int q = lane; q < m; q += 32) v += Ak[q] * za[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sV[k * 64 + a] = v;
+  }
+  __syncthreads();
+  for (int c = tid; c < RB; c += nt) {
+    T acc = T(0);
+    if (c < r)
+      for (int k = 0; k < nk; ++k)
+        for (int a = 0; a < r; ++a) acc += sV[k * 64 + a] * T(G[((long long)k * RB + a) * RB + c]);
+    out[(long long)c * m + p] = y[(long long)c * m + p] + beta * acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Gram reduction: out[j * lda_out + a] += sum_rows A(row, a) F(row, j),
 // 64 x 64 output tiles, 32-row chunks, FP32/FP64 per-thread accumulation with
 // compensated summation across chunks, FP64 atomics at the end.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FPlain {  // F(row, j) = B[j * ldb + row], zero for j >= jdim
+  static constexpr bool kTables = false;
+  __device__ void prep(int*, T*, long long, long long) const {}
   const T* B;
   long long ldb;
   const int* jdim;
   int jcap;
-  __device__ T operator()(long long r, int j, int jact) const { return j < jact ? B[(long long)j * ldb + r] : T(0); }
+  __device__ T operator()(long long r, int j, int jact, int, const int*, const T*) const {
+    return j < jact ? B[(long long)j * ldb + r] : T(0);
+  }
   __device__ int jact() const { return dev_dim(jdim, jcap); }
 };
 
 template <typename T>
 struct FDiag {  // F(row, k * nb + b) = wv[k * n + row] * B[b * ldb + row]
+  static constexpr bool kTables = false;
+  __device__ void prep(int*, T*, long long, long long) const {}
   const T* B;
   long long ldb;
   const T* wv;
@@ -304,42 +424,57 @@ struct FDiag {  // F(row, k * nb + b) = wv[k * n + row] * B[b * ldb + row]
   int nb;
   const int* bdim;
   int nk;
-  __device__ T operator()(long long r, int j, int bact) const {
+  __device__ T operator()(long long r, int j, int bact, int, const int*, const T*) const {
     int k = j / nb, b = j - k * nb;
     return (k < nk && b < bact) ? wv[(long long)k * n + r] * B[(long long)b * ldb + r] : T(0);
   }
   __device__ int jact() const { return dev_dim(bdim, nb); }
 };
 
+constexpr int GR_TC = 32;
+
 template <typename T>
-struct FStencil {  // F(row, k * nb + b) = D_k(rho^-1 B[:, b])(row)
+struct FStencil {  // F(row, k * nb + b) = D_k(rho^-1 B[:, b])(row), tables per row chunk
+  static constexpr bool kTables = true;
   const T* B;
   long long ldb;
   const T* inv_rho;
   Geo g;
   int nb;
   const int* bdim;
-  __device__ T operator()(long long r, int j, int bact) const {
+  __device__ void prep(int* sOff, T* sR, long long r0, long long rows) const {
+    stencil_tables<T, GR_TC>(sOff, sR, r0, rows, inv_rho, g);
+  }
+  __device__ T operator()(long long r, int j, int bact, int t, const int* sOff, const T* sR) const {
     int k = j / nb, b = j - k * nb;
     if (k >= 2 * g.nact || b >= bact) return T(0);
-    int ix, iy, iz;
-    cell_coords(r, g, ix, iy, iz);
-    return stencil_value(B + (long long)b * ldb, inv_rho, r, ix, iy, iz, k, g);
+    const int da = k >> 1, s = k & 1;
+    const int d = g.dirs[da];
+    const int base = 1 + 4 * d + 2 * s;
+    const T* col = B + (long long)b * ldb + r;
+    const T v0 = col[0] * sR[t];
+    const T v1 = col[sOff[base * GR_TC + t]] * sR[base * GR_TC + t];
+    const T v2 = col[sOff[(base + 1) * GR_TC + t]] * sR[(base + 1) * GR_TC + t];
+    const T inv = T(g.inv2d[d]);
+    return s == 0 ? (T(-3) * v0 + T(4) * v1 - v2) * inv : (T(3) * v0 - T(4) * v1 + v2) * inv;
   }
   __device__ int jact() const { return dev_dim(bdim, nb); }
 };
 
-constexpr int GR_TC = 32;
 
-template <typename T, class F>
+
+template <typename T, class F, int TILE>
 __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __restrict__ A, long long lda,
                                                    const int* adim, int acap, int ncols_j, F f,
                                                    double* __restrict__ out, long long ldo) {
-  __shared__ T sA[GR_TC][65];
-  __shared__ T sF[GR_TC][65];
+  constexpr int TPD = TILE / 4;  // threads per tile dimension, 4 x 4 outputs each
+  __shared__ T sA[GR_TC][TILE + 1];
+  __shared__ T sF[GR_TC][TILE + 1];
+  __shared__ int sOff[F::kTables ? 13 * GR_TC : 1];
+  __shared__ T sR[F::kTables ? 13 * GR_TC : 1];
   const int tid = threadIdx.x;
-  const int ta = tid % 16, tj = tid / 16;
-  const int a0 = blockIdx.y * 64, j0 = blockIdx.z * 64;
+  const int ta = tid % TPD, tj = tid / TPD;
+  const int a0 = blockIdx.y * TILE, j0 = blockIdx.z * TILE;
   const int Aact = dev_dim(adim, acap);
   const int Jact = f.jact();
   T acc[4][4], cmp[4][4];
@@ -348,12 +483,16 @@ __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); cmp[i][j] = T(0); }
   for (long long r0 = (long long)blockIdx.x * GR_TC; r0 < rows; r0 += (long long)gridDim.x * GR_TC) {
-    for (int e = tid; e < GR_TC * 64; e += blockDim.x) {
+    if (F::kTables) {
+      f.prep(sOff, sR, r0, rows);
+      __syncthreads();
+    }
+    for (int e = tid; e < GR_TC * TILE; e += blockDim.x) {
       int t = e % GR_TC, c = e / GR_TC;
       long long r = r0 + t;
       int a = a0 + c, j = j0 + c;
       sA[t][c] = (r < rows && a < Aact && a < acap) ? A[(long long)a * lda + r] : T(0);
-      sF[t][c] = (r < rows && j < ncols_j) ? f(r, j, Jact) : T(0);
+      sF[t][c] = (r < rows && j < ncols_j) ? f(r, j, Jact, t, sOff, sR) : T(0);
     }
     __syncthreads();
     T p[4][4];
@@ -365,9 +504,9 @@ __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __re
     for (int t = 0; t < GR_TC; ++t) {
       T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[t][ta + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = sA[t][ta + TPD * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sF[t][tj + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = sF[t][tj + TPD * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -387,11 +526,11 @@ __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __re
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    int a = a0 + ta + 16 * i;
+    int a = a0 + ta + TPD * i;
     if (a >= acap) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int jj = j0 + tj + 16 * j;
+      int jj = j0 + tj + TPD * j;
       if (jj >= ncols_j) continue;
       double v = (double)acc[i][j] - (double)cmp[i][j];
       if (v != 0.0) atomicAdd(out + (long long)jj * ldo + a, v);

@@ -156,7 +156,7 @@ __device__ __forceinline__ void rr_pair(int round, int i, int n, int& a, int& b)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
+__global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
                                  double* __restrict__ P, double* __restrict__ Q, double* __restrict__ S,
                                  BeamDims* dims, int* rank_log, int* err) {
   extern __shared__ __align__(16) unsigned char raw[];
@@ -305,7 +305,7 @@ void launch_svd_truncate(cudaStream_t st, const double* Sh, int n2, int RB, Rank
                          double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err) {
   size_t smem = (size_t)2 * n2 * n2 * sizeof(T);
   if (smem > 48 * 1024) cudaFuncSetAttribute(svd_trunc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  svd_trunc_kernel<T><<<1, 512, smem, st>>>(Sh, n2, RB, rp, step, event, P, Q, S, dims, rank_log, err);
+  svd_trunc_kernel<T><<<1, 1024, smem, st>>>(Sh, n2, RB, rp, step, event, P, Q, S, dims, rank_log, err);
 }
 template void launch_svd_truncate<float>(cudaStream_t, const double*, int, int, RankParams, int, int, double*, double*,
                                          double*, BeamDims*, int*, int*);
@@ -315,63 +315,110 @@ template void launch_svd_truncate<double>(cudaStream_t, const double*, int, int,
 // ---------------------------------------------------------------------------
 // Galerkin S-step with RK4 in Horner form
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(1024) sstep_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph, int nk,
-                             const double* __restrict__ S, int RB, int n2, const double* __restrict__ beta, int nsub,
-                             double* __restrict__ Sh) {
+// Each thread owns an MT x MT tile of the n2 x n2 result; the products z P_k and
+// G_k (z P_k) run from shared memory. The 2 nk operators are preloaded once when
+// they fit, otherwise reloaded per k.
+template <typename T, int MT>
+__global__ void __launch_bounds__(1024) sstep_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph,
+                                                     int nk, const double* __restrict__ S, int RB, int n2,
+                                                     const double* __restrict__ beta, int nsub, int preload,
+                                                     double* __restrict__ Sh) {
   extern __shared__ __align__(16) unsigned char raw[];
-  T* z = reinterpret_cast<T*>(raw);
-  T* tmp = z + n2 * n2;
-  const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = n2 * n2;
-  constexpr int EPT = 16;
+  T* z = reinterpret_cast<T*>(raw);   // stage input, col-major
+  T* tmp = z + ne;                    // z P_k
+  T* ops = tmp + ne;                  // preload: [P_0..P_{nk-1}, G_0..G_{nk-1}]; else 1 slot
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nb = n2 / MT;             // tiles per dimension
+  const int ti = tid % nb, tj = tid / nb;
+  const bool owner = tj < nb;
   for (int e = tid; e < ne; e += nt) {
     int a = e % n2, c = e / n2;
     double y = (a < RB && c < RB) ? S[c * RB + a] : 0.0;
     Sh[e] = y;
     z[e] = T(y);
   }
+  if (preload) {
+    for (int e = tid; e < nk * ne; e += nt) {
+      ops[e] = T(Ph[e]);
+      ops[nk * ne + e] = T(Gh[e]);
+    }
+  }
   __syncthreads();
   for (int j = 0; j < nsub; ++j) {
     for (int s = 0; s < 4; ++s) {
       const double b = beta[4 * j + s];
-      T acc[EPT];
+      T acc[MT][MT];
 #pragma unroll
-      for (int i = 0; i < EPT; ++i) acc[i] = T(0);
+      for (int u = 0; u < MT; ++u)
+#pragma unroll
+        for (int v = 0; v < MT; ++v) acc[u][v] = T(0);
       for (int k = 0; k < nk; ++k) {
-        const double* Pk = Ph + (long long)k * n2 * n2;
-        const double* Gk = Gh + (long long)k * n2 * n2;
+        const T* Pk;
+        const T* Gk;
+        if (preload) {
+          Pk = ops + (long long)k * ne;
+          Gk = ops + (long long)(nk + k) * ne;
+        } else {
+          for (int e = tid; e < ne; e += nt) ops[e] = T(Ph[(long long)k * ne + e]);
+          __syncthreads();
+          Pk = ops;
+          Gk = ops;
+        }
+        // tmp = z Pk
+        if (owner) {
+          T t[MT][MT];
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-          int e = tid + i * nt;
-          if (e < ne) {
-            int a = e % n2, c = e / n2;
-            T t = 0;
-            for (int q = 0; q < n2; ++q) t += z[q * n2 + a] * T(Pk[c * n2 + q]);
-            tmp[e] = t;
+          for (int u = 0; u < MT; ++u)
+#pragma unroll
+            for (int v = 0; v < MT; ++v) t[u][v] = T(0);
+          for (int q = 0; q < n2; ++q) {
+            T za[MT], pb[MT];
+#pragma unroll
+            for (int u = 0; u < MT; ++u) za[u] = z[q * n2 + ti + u * nb];
+#pragma unroll
+            for (int v = 0; v < MT; ++v) pb[v] = Pk[(tj + v * nb) * n2 + q];
+#pragma unroll
+            for (int u = 0; u < MT; ++u)
+#pragma unroll
+              for (int v = 0; v < MT; ++v) t[u][v] += za[u] * pb[v];
           }
+#pragma unroll
+          for (int u = 0; u < MT; ++u)
+#pragma unroll
+            for (int v = 0; v < MT; ++v) tmp[(tj + v * nb) * n2 + ti + u * nb] = t[u][v];
         }
         __syncthreads();
+        if (!preload) {
+          for (int e = tid; e < ne; e += nt) ops[e] = T(Gh[(long long)k * ne + e]);
+          __syncthreads();
+        }
+        // acc += Gk tmp
+        if (owner) {
+          for (int q = 0; q < n2; ++q) {
+            T ga[MT], tb[MT];
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-          int e = tid + i * nt;
-          if (e < ne) {
-            int a = e % n2, c = e / n2;
-            T t = 0;
-            for (int q = 0; q < n2; ++q) t += T(Gk[q * n2 + a]) * tmp[c * n2 + q];
-            acc[i] += t;
+            for (int u = 0; u < MT; ++u) ga[u] = Gk[q * n2 + ti + u * nb];
+#pragma unroll
+            for (int v = 0; v < MT; ++v) tb[v] = tmp[(tj + v * nb) * n2 + q];
+#pragma unroll
+            for (int u = 0; u < MT; ++u)
+#pragma unroll
+              for (int v = 0; v < MT; ++v) acc[u][v] += ga[u] * tb[v];
           }
         }
         __syncthreads();
       }
+      if (owner) {
 #pragma unroll
-      for (int i = 0; i < EPT; ++i) {
-        int e = tid + i * nt;
-        if (e < ne) {
-          double nv = Sh[e] + b * (double)acc[i];
-          if (s == 3) Sh[e] = nv;
-          z[e] = T(nv);
-        }
+        for (int u = 0; u < MT; ++u)
+#pragma unroll
+          for (int v = 0; v < MT; ++v) {
+            int e = (tj + v * nb) * n2 + ti + u * nb;
+            double nv = Sh[e] + b * (double)acc[u][v];
+            if (s == 3) Sh[e] = nv;
+            z[e] = T(nv);
+          }
       }
       __syncthreads();
     }
@@ -381,9 +428,21 @@ __global__ void __launch_bounds__(1024) sstep_kernel(const double* __restrict__ 
 template <typename T>
 void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
                   const double* beta, int nsub, double* Sh) {
-  size_t smem = (size_t)2 * n2 * n2 * sizeof(T);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(sstep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  sstep_kernel<T><<<1, 1024, smem, st>>>(Gh, Ph, nk, S, RB, n2, beta, nsub, Sh);
+  const size_t ne = (size_t)n2 * n2;
+  const size_t full = (2 + 2 * (size_t)nk) * ne * sizeof(T);
+  const int preload = full <= 200 * 1024 ? 1 : 0;
+  const size_t smem = preload ? full : 3 * ne * sizeof(T);
+  if (n2 <= 64) {
+    const int nb = n2 / 2;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(sstep_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sstep_kernel<T, 2><<<1, nb * nb, smem, st>>>(Gh, Ph, nk, S, RB, n2, beta, nsub, preload, Sh);
+  } else {
+    const int nb = n2 / 4;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(sstep_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sstep_kernel<T, 4><<<1, nb * nb, smem, st>>>(Gh, Ph, nk, S, RB, n2, beta, nsub, preload, Sh);
+  }
 }
 template void launch_sstep<float>(cudaStream_t, const double*, const double*, int, const double*, int, int,
                                   const double*, int, double*);
