@@ -52,6 +52,17 @@ __global__ void pstack_kernel(const double* __restrict__ P, int RB, int nk, T* _
 }
 
 template <typename T>
+__global__ void gt_kernel(const double* __restrict__ G, int RB, int nk, T* __restrict__ GT) {
+  // GT[(k*RB + c)*RB + a] = G_k[c][a] = G[(k*RB + a)*RB + c]
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int tot = nk * RB * RB;
+  if (e >= tot) return;
+  int a = e % RB, j = e / RB;
+  int k = j / RB, c = j % RB;
+  GT[e] = T(G[((long long)k * RB + a) * RB + c]);
+}
+
+template <typename T>
 __global__ void src_vec_kernel(const T* __restrict__ w, const double* __restrict__ psi, long long n, int M,
                                T* __restrict__ A) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,6 +157,69 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
   ++nl;
 }
 
+// rank capacities with a compiled streaming-stage kernel
+constexpr int kRankCaps[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
+
+template <typename T, int RM, int NACT>
+void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
+                   const Geo& g, const T* Pst, const int* rdim, T beta, int last) {
+  size_t smem = (size_t)2 * NACT * RM * RM * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kstage_kernel<T, RM, NACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kstage_kernel<T, RM, NACT><<<nblk(n, 128), 128, smem, st>>>(vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta,
+                                                              last);
+}
+
+template <typename T, int NACT>
+void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n,
+                     const T* inv_rho, const Geo& g, const T* Pst, const int* rdim, T beta, int last) {
+  switch (RB) {
+#define KS_CASE(R) \
+  case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last); break;
+    KS_CASE(4) KS_CASE(8) KS_CASE(12) KS_CASE(16) KS_CASE(20) KS_CASE(24) KS_CASE(32)
+    KS_CASE(40) KS_CASE(48) KS_CASE(64)
+#undef KS_CASE
+    default: break;
+  }
+}
+
+// one RK4 Horner stage of the K-step on the scaled input vin = rho^-1 z
+template <typename T>
+void kstage(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
+            const Geo& g, const T* Pst, const int* rdim, T beta, int last, int64_t& nl) {
+  if (g.nact == 3) kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last);
+  else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last);
+  ++nl;
+}
+
+// out[(k*ldj + b)*ldo + a] += sum_i A(i, a) D_k(rho^-1 B(:, b))(i)
+template <typename T>
+void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, int na, const int* adim, const T* B,
+                  long long ldb, int nb, const int* bdim, const T* inv_rho, const Geo& g, double* out, int ldj,
+                  long long ldo, int64_t& nl) {
+  const int nk = 2 * g.nact;
+  const int nj = nk * nb;
+  const int naP = (na + 3) / 4 * 4;
+  const int tpa = naP / 4;
+  int jslice = std::min((nj + 7) / 8 * 8, std::max(8, (512 / tpa) / 1 * 8));
+  jslice = std::min(jslice, (512 / tpa) * 8);
+  const int nslice = (nj + jslice - 1) / jslice;
+  const int threads = tpa * ((std::min(jslice, nj) + 7) / 8);
+  const int ldA = naP + (((naP / 4) & 1) ? 0 : 4);
+  const int ldS = jslice + (((jslice / 4) & 1) ? 0 : 4);
+  const size_t smem = (size_t)GS_TC * (ldA + ldS) * sizeof(T) + (size_t)13 * GS_TC * (sizeof(int) + sizeof(T));
+  const long long chunks = (rows + GS_TC - 1) / GS_TC;
+  auto kern = g.nact == 3 ? gram_stencil_kernel<T, 3> : gram_stencil_kernel<T, 2>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  per_sm = std::max(per_sm, 1);
+  const int gx = (int)std::max(1LL, std::min(chunks, (long long)std::max(1, 152 * per_sm / nslice)));
+  kern<<<dim3(gx, nslice), threads, smem, st>>>(rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, jslice, out,
+                                                ldj, ldo);
+  ++nl;
+}
+
 // ---------------------------------------------------------------------------
 // engine state
 // ---------------------------------------------------------------------------
@@ -204,6 +278,7 @@ struct dlra_ctx {
   void *inv_rho = nullptr, *wc = nullptr, *wT = nullptr, *Apm = nullptr;
   void *Kb[3] = {nullptr, nullptr, nullptr}, *Xh = nullptr, *Asrc = nullptr;
   void *Lb[3] = {nullptr, nullptr, nullptr}, *Zm = nullptr, *Wh = nullptr, *L1T = nullptr, *Pst = nullptr;
+  void* GtT = nullptr;
   double *rho = nullptr, *f_cell = nullptr, *tau_cell = nullptr;
   double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
   double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr, *Gt = nullptr;
@@ -413,14 +488,15 @@ struct Engine {
     ++nl;
     // G_k = X^T D_k rho^-1 X
     cudaMemsetAsync(ctx->G1, 0, sizeof(double) * nk * RB * RB, st);
-    gram<T>(st, n, B.X, n, rdim, RB, nk * RB, FStencil<T>{B.X, n, P(ctx->inv_rho), ctx->geo, RB, rdim}, ctx->G1, RB,
-            nl);
-    // K-step: K0 = X S, RK4 Horner stages z <- y + beta L(z)
+    gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, ctx->G1, RB, RB, nl);
+    gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->G1, RB, nk, P(ctx->GtT));
+    ++nl;
+    // K-step: K0 = X S (and rho^-1 K0), RK4 Horner stages z <- y + beta L(z) on scaled inputs
     T* y = P(ctx->Kb[0]);
-    T* za = P(ctx->Kb[1]);
-    T* zb = P(ctx->Kb[2]);
+    T* va = P(ctx->Kb[1]);
+    T* vb = P(ctx->Kb[2]);
     gemm<T, 16>(st, n, RB, RB, ALoadPlain<T>{B.X, n, rdim, RB}, BLoadCol<T, double>{B.S, RB, nullptr, RB, nullptr, RB},
-                EpiStore<T>{y, n, nullptr, n, T(1), T(0)}, nl);
+                EpiStoreScaled<T>{y, va, n, P(ctx->inv_rho)}, nl);
     // L-step: L0 = W S^T
     T* ly = P(ctx->Lb[0]);
     T* la = P(ctx->Lb[1]);
@@ -432,19 +508,24 @@ struct Engine {
     for (int j = 0; j < ns; ++j) {
       double beta[4];
       horner_betas(ctx, ctx->E[k] - j * hs, hs, beta);
-      const T* zin = y;
-      T* outs[4] = {za, zb, za, y};
+      const T* vins[4] = {va, vb, va, vb};
+      T* vouts[4] = {vb, va, vb, va};
       const T* lin = ly;
       T* louts[4] = {la, lb, la, ly};
       for (int s = 0; s < 4; ++s) {
         prof_begin(ctx);
-        gemm<T, 24>(st, n, RB, nk * RB, ALoadStencil<T>{zin, n, P(ctx->inv_rho), ctx->geo, rdim, RB},
-                    BLoadRow<T, T>{P(ctx->Pst), RB, nk * RB, RB}, EpiKStage<T>{outs[s], y, n, T(beta[s])}, nl);
+        kstage<T>(RB, st, vins[s], y, y, vouts[s], n, P(ctx->inv_rho), ctx->geo, P(ctx->Pst), rdim, T(beta[s]),
+                  s == 3 ? 1 : 0, nl);
         prof_end(ctx);
-        zin = outs[s];
         // m-side: out = y + beta sum_k A^s_d z G_k^T
-        lstage_kernel<T><<<m, 128, 0, st>>>(P(ctx->Apm), m, nk, lin, ly, louts[s], ctx->G1, RB, rdim, T(beta[s]));
-        ++nl;
+        {
+          const size_t smem = ((size_t)nk * m + (size_t)nk * RB * RB + (size_t)(128 / (RB <= 32 ? 32 : 64)) * nk * RB) * sizeof(T);
+          if (smem > 48 * 1024)
+            cudaFuncSetAttribute(lstage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          lstage_kernel<T><<<m, 128, smem, st>>>(P(ctx->Apm), m, nk, lin, ly, louts[s], P(ctx->GtT), RB, rdim,
+                                                T(beta[s]));
+          ++nl;
+        }
         lin = louts[s];
       }
     }
@@ -456,8 +537,7 @@ struct Engine {
     T* Xh = P(ctx->Xh);
     T* Wh = P(ctx->Wh);
     cudaMemsetAsync(ctx->Gc, 0, sizeof(double) * nk * n2 * n2, st);
-    gram<T>(st, n, Xh, n, nullptr, n2, nk * n2, FStencil<T>{Xh, n, P(ctx->inv_rho), ctx->geo, n2, nullptr}, ctx->Gc,
-            n2, nl);
+    gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, ctx->Gc, n2, n2, nl);
     gemm<T, 16>(st, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{Wh, m, nullptr, m, nullptr, n2}, EpiStoreKBlocks<T>{Zm, m, n2}, nl);
     cudaMemsetAsync(ctx->Ph, 0, sizeof(double) * nk * n2 * n2, st);
@@ -569,6 +649,7 @@ dlra_status alloc_shared(dlra_ctx* ctx) {
   ALLOC(ctx->Wh, sizeof(T) * (size_t)m * n2);
   ALLOC(ctx->L1T, sizeof(T) * (size_t)m * RB);
   ALLOC(ctx->Pst, sizeof(T) * (size_t)nk * RB * RB);
+  ALLOC(ctx->GtT, sizeof(T) * (size_t)nk * RB * RB);
   ALLOC(ctx->Apm, sizeof(T) * (size_t)nk * m * m);
   ALLOC(ctx->G1, sizeof(double) * nk * RB * RB);
   ALLOC(ctx->P1, sizeof(double) * nk * RB * RB);
@@ -961,8 +1042,9 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
   ctx->N = g.sh_degree;
   ctx->m = (g.sh_degree + 1) * (g.sh_degree + 1);
   ctx->K = g.n_energy_steps;
-  ctx->RB = (g.rank_max + 3) / 4 * 4;
-  if (ctx->RB > 64) ctx->RB = 64;
+  ctx->RB = 64;
+  for (int cap : kRankCaps)
+    if (cap >= g.rank_max) { ctx->RB = cap; break; }
   ctx->n2 = 2 * ctx->RB;
   const size_t tsz = ctx->fp64 ? 8 : 4;
   if ((size_t)ctx->m * ctx->RB * tsz > 160 * 1024)

@@ -359,37 +359,281 @@ __global__ void __launch_bounds__(256) gemm_kernel(long long rows, int N, int Q,
 }
 
 // ---------------------------------------------------------------------------
+// Fused streaming stage of the K-step (Sec. 3.3.2-3.3.3), one thread per cell:
+//   out(i, :) = y(i, :) + beta * sum_c sum_k D_k(rho^-1 z(:, c))(i) P_k[c][:]
+// with the r outputs in registers, the neighbour offsets and rho^-1 of the 13
+// stencil points in registers, and the stacked P (row (c*nk + k), RM columns) in
+// shared memory read as broadcasts.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float* p, float* v) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double* p, double* v) {
+    double2 a = *reinterpret_cast<const double2*>(p);
+    double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+template <typename T, int RM, int NACT>
+__global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, const T* __restrict__ y,
+                                                     T* __restrict__ yout, T* __restrict__ vout, long long ld,
+                                                     const T* __restrict__ inv_rho, Geo g, const T* __restrict__ Pst,
+                                                     const int* __restrict__ rdim, T beta, int last) {
+  // vin = rho^-1 z (scaled stage input). last = 0: vout = rho^-1 (y + beta acc);
+  // last = 1: yout = y + beta acc and vout = rho^-1 yout (input of the next sub-step).
+  constexpr int NK = 2 * NACT;
+  constexpr int NP = 1 + 4 * NACT;
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* sP = reinterpret_cast<T*>(raw);
+  const int r = dev_dim(rdim, RM);
+  for (int e = threadIdx.x; e < NK * RM * r; e += blockDim.x) sP[e] = Pst[e];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int ii = (int)i, nxy = (int)g.nxy;
+  const int iz = ii / nxy, rem = ii - iz * nxy;
+  const int iy = rem / g.nx, ix = rem - iy * g.nx;
+  // neighbour validity bits (m1, m2, p1, p2 per direction) and strides
+  unsigned valid = 0;
+  int stv[NACT];
+#pragma unroll
+  for (int da = 0; da < NACT; ++da) {
+    const int d = (NACT == 3) ? da : (da == 0 ? 0 : 2);
+    const int c = d == 0 ? ix : (d == 1 ? iy : iz);
+    const int L = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    stv[da] = d == 0 ? 1 : (d == 1 ? g.nx : nxy);
+    valid |= (unsigned)(c >= 1) << (4 * da);
+    valid |= (unsigned)(c >= 2) << (4 * da + 1);
+    valid |= (unsigned)(c + 1 < L) << (4 * da + 2);
+    valid |= (unsigned)(c + 2 < L) << (4 * da + 3);
+  }
+  T inv2[NACT];
+#pragma unroll
+  for (int da = 0; da < NACT; ++da) inv2[da] = T(g.inv2d[(NACT == 3) ? da : (da == 0 ? 0 : 2)]);
+  T acc[RM];
+#pragma unroll
+  for (int c = 0; c < RM; ++c) acc[c] = T(0);
+  for (int c = 0; c < r; ++c) {
+    const T* col = vin + (long long)c * ld + i;
+    T v[NP];
+    v[0] = col[0];
+#pragma unroll
+    for (int da = 0; da < NACT; ++da) {
+      const int st = stv[da];
+      v[1 + 4 * da] = (valid >> (4 * da)) & 1u ? col[-st] : T(0);
+      v[2 + 4 * da] = (valid >> (4 * da + 1)) & 1u ? col[-2 * st] : T(0);
+      v[3 + 4 * da] = (valid >> (4 * da + 2)) & 1u ? col[st] : T(0);
+      v[4 + 4 * da] = (valid >> (4 * da + 3)) & 1u ? col[2 * st] : T(0);
+    }
+    T sv[NK];
+#pragma unroll
+    for (int da = 0; da < NACT; ++da) {
+      sv[2 * da] = (T(-3) * v[0] + T(4) * v[1 + 4 * da] - v[2 + 4 * da]) * inv2[da];
+      sv[2 * da + 1] = (T(3) * v[0] - T(4) * v[3 + 4 * da] + v[4 + 4 * da]) * inv2[da];
+    }
+    const T* Pc = sP + (long long)c * NK * RM;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+#pragma unroll
+      for (int cp = 0; cp < RM; cp += 4) {
+        T p4[4];
+        Vec4<T>::load(Pc + k * RM + cp, p4);
+        acc[cp] += sv[k] * p4[0];
+        acc[cp + 1] += sv[k] * p4[1];
+        acc[cp + 2] += sv[k] * p4[2];
+        acc[cp + 3] += sv[k] * p4[3];
+      }
+    }
+  }
+  const T ir0 = inv_rho[i];
+  if (last) {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      const T yn = y[(long long)c * ld + i] + beta * acc[c];
+      yout[(long long)c * ld + i] = yn;
+      vout[(long long)c * ld + i] = ir0 * yn;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) vout[(long long)c * ld + i] = ir0 * (y[(long long)c * ld + i] + beta * acc[c]);
+  }
+}
+
+template <typename T>
+struct EpiStoreScaled {  // C = acc and V = rho^-1 acc
+  T* C;
+  T* V;
+  long long ldc;
+  const T* inv_rho;
+  __device__ void operator()(long long r, int c, T acc) const {
+    C[(long long)c * ldc + r] = acc;
+    V[(long long)c * ldc + r] = inv_rho[r] * acc;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Stencil Gram G_k[a][b] = sum_i A(i, a) D_k(rho^-1 B(:, b))(i), k = 2 da + s,
+// written at out[(k * ldj + b) * ldo + a]. A block takes a 64-cell chunk at a time,
+// stages A and the nk stencil values of every B column in shared memory (13 loads
+// per column and cell) and accumulates 4 x 8 register tiles of the (a, j = k nb + b)
+// output with compensated sums across chunks.
+// ---------------------------------------------------------------------------
+constexpr int GS_TC = 64;
+
+template <typename T, int NACT>
+__global__ void __launch_bounds__(512) gram_stencil_kernel(long long rows, const T* __restrict__ A, long long lda, int na,
+                                                           const int* adim, const T* __restrict__ B, long long ldb,
+                                                           int nb, const int* bdim, const T* __restrict__ inv_rho,
+                                                           Geo g, int jslice, double* __restrict__ out, int ldj,
+                                                           long long ldo) {
+  constexpr int NK = 2 * NACT;
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int nj = NK * nb;
+  const int naP = (na + 3) / 4 * 4;
+  // row pitches padded to an odd number of 16-byte groups (fewer bank conflicts)
+  const int ldA = naP + (((naP / 4) & 1) ? 0 : 4);
+  const int ldS = jslice + (((jslice / 4) & 1) ? 0 : 4);
+  T* sA = reinterpret_cast<T*>(raw);            // [GS_TC][ldA]
+  T* sS = sA + GS_TC * ldA;                     // [GS_TC][ldS]
+  int* sOff = reinterpret_cast<int*>(sS + GS_TC * ldS);  // [13][GS_TC]
+  T* sR = reinterpret_cast<T*>(sOff + 13 * GS_TC);
+  const int tid = threadIdx.x;
+  const int tpa = naP / 4;                     // threads along a
+  const int ta = tid % tpa, tj = tid / tpa;    // tile (a: 4, j: 8)
+  const int j0 = blockIdx.y * jslice;
+  const int jn = min(jslice, nj - j0);
+  const bool owner = tj * 8 < jn;
+  const int Aact = dev_dim(adim, na), Bact = dev_dim(bdim, nb);
+  T acc[4][8];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = T(0);
+  for (long long r0 = (long long)blockIdx.x * GS_TC; r0 < rows; r0 += (long long)gridDim.x * GS_TC) {
+    stencil_tables<T, GS_TC>(sOff, sR, r0, rows, inv_rho, g);
+    for (int e = tid; e < GS_TC * naP; e += blockDim.x) {
+      int t = e % GS_TC, a = e / GS_TC;
+      long long rr = r0 + t;
+      sA[t * ldA + a] = (rr < rows && a < Aact) ? A[(long long)a * lda + rr] : T(0);
+    }
+    __syncthreads();
+    // stencil values: item (b, t) for every b whose columns j = k*nb + b fall in the slice
+    for (int e = tid; e < GS_TC * nb; e += blockDim.x) {
+      int t = e % GS_TC, b = e / GS_TC;
+      long long rr = r0 + t;
+      T sv[NK];
+      if (rr < rows && b < Bact) {
+        stencil_values<T, GS_TC>(B + (long long)b * ldb + rr, sOff, sR, t, g, sv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) sv[k] = T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        int jl = k * nb + b - j0;
+        if (jl >= 0 && jl < jslice) sS[t * ldS + jl] = sv[k];
+      }
+    }
+    __syncthreads();
+    if (owner) {
+#pragma unroll 4
+      for (int t = 0; t < GS_TC; ++t) {
+        T a4[4], b8[8];
+        Vec4<T>::load(sA + t * ldA + ta * 4, a4);
+        Vec4<T>::load(sS + t * ldS + tj * 8, b8);
+        Vec4<T>::load(sS + t * ldS + tj * 8 + 4, b8 + 4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] += a4[u] * b8[v];
+      }
+    }
+    __syncthreads();
+  }
+  if (!owner) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = ta * 4 + u;
+    if (a >= na) continue;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int j = j0 + tj * 8 + v;
+      if (j >= nj || tj * 8 + v >= jn) continue;
+      const int k = j / nb, b = j - k * nb;
+      double val = (double)acc[u][v];
+      if (val != 0.0) atomicAdd(out + ((long long)k * ldj + b) * ldo + a, val);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // m-side RK4 stage of the L-step: out = y + beta * sum_k Apm_k z G_k^T
 // (Apm_k = A^s_d row-major m x m, G_k at G[(k*RB + b)*RB + a] = G_k[a][b]).
 // Each block owns LS_RPB rows: V_k = Apm_k(rows, :) z, acc += V_k G_k^T.
 // ---------------------------------------------------------------------------
-// One block per moment row p: V_k(a) = Apm_k[p, :] z(:, a) by warp dot products,
-// then out(p, c) = y(p, c) + beta sum_k sum_a V_k(a) G_k[c][a].
+// One block per moment row p. The rows p of the nk operators and the G_k (as T,
+// GT[(k*RB + c)*RB + a] = G_k[c][a]) are staged in shared memory; thread (a, g)
+// forms the partial dot products V_k(a) = sum_q Apm_k[p][q] z(q, a) over its
+// quarter (or half) of q, then out(p, c) = y(p, c) + beta sum_k sum_a V_k(a) G_k[c][a].
 template <typename T>
 __global__ void __launch_bounds__(128) lstage_kernel(const T* __restrict__ Apm, int m, int nk,
                                                      const T* __restrict__ z, const T* __restrict__ y,
-                                                     T* __restrict__ out, const double* __restrict__ G, int RB,
+                                                     T* __restrict__ out, const T* __restrict__ GT, int RB,
                                                      const int* __restrict__ rdim, T beta) {
-  __shared__ T sV[6 * 64];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* sA = reinterpret_cast<T*>(raw);     // nk x m
+  T* sG = sA + nk * m;                   // nk x RB x RB
+  T* sP = sG + nk * RB * RB;             // groups x nk x RB partial sums
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int r = dev_dim(rdim, RB);
   const int p = blockIdx.x;
-  for (int pr = wid; pr < nk * r; pr += nw) {
-    const int k = pr / r, a = pr - k * r;
-    const T* Ak = Apm + ((long long)k * m + p) * m;
+  for (int e = tid; e < nk * m; e += nt) {
+    const int k = e / m, q = e - k * m;
+    sA[e] = Apm[((long long)k * m + p) * m + q];
+  }
+  for (int e = tid; e < nk * RB * RB; e += nt) sG[e] = GT[e];
+  __syncthreads();
+  const int aw = RB <= 32 ? 32 : 64;
+  const int groups = nt / aw;
+  const int a = tid % aw, g = tid / aw;
+  const int q0 = (m * g) / groups, q1 = (m * (g + 1)) / groups;
+  if (a < r) {
+    T part[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const T* za = z + (long long)a * m;
-    T v = T(0);
-    for (int q = lane; q < m; q += 32) v += Ak[q] * za[q];
+#pragma unroll 4
+    for (int q = q0; q < q1; ++q) {
+      const T zv = za[q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sV[k * 64 + a] = v;
+      for (int k = 0; k < 6; ++k)
+        if (k < nk) part[k] += sA[k * m + q] * zv;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < nk) sP[(g * nk + k) * RB + a] = part[k];
+  } else if (a < RB) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < nk) sP[(g * nk + k) * RB + a] = T(0);
   }
   __syncthreads();
   for (int c = tid; c < RB; c += nt) {
     T acc = T(0);
     if (c < r)
       for (int k = 0; k < nk; ++k)
-        for (int a = 0; a < r; ++a) acc += sV[k * 64 + a] * T(G[((long long)k * RB + a) * RB + c]);
+        for (int aa = 0; aa < r; ++aa) {
+          T v = T(0);
+          for (int gg = 0; gg < groups; ++gg) v += sP[(gg * nk + k) * RB + aa];
+          acc += v * sG[(k * RB + c) * RB + aa];
+        }
     out[(long long)c * m + p] = y[(long long)c * m + p] + beta * acc;
   }
 }

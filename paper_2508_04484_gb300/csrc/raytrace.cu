@@ -150,7 +150,8 @@ __global__ void raytrace_kernel(const double* __restrict__ rays, int nray, RayGe
 void launch_raytrace(cudaStream_t st, const double* rays, int nray, RayGeo g, const double* f_cell,
                      const double* tau_cell, double* psi, double* e_u) {
   if (nray <= 0) return;
-  raytrace_kernel<<<(nray + 127) / 128, 128, 0, st>>>(rays, nray, g, f_cell, tau_cell, psi, e_u);
+  // few, long-running threads: small blocks spread the rays over all SMs
+  raytrace_kernel<<<(nray + 31) / 32, 32, 0, st>>>(rays, nray, g, f_cell, tau_cell, psi, e_u);
 }
 
 }  // namespace dlra

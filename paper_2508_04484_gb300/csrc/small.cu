@@ -164,14 +164,28 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
   T* V = A + n2 * n2;
   __shared__ double sig[128];
   __shared__ int order[128];
+  __shared__ T nrm[128];   // squared column norms, updated by each rotation
+  __shared__ T red[32];
   __shared__ int s_rot, s_r1;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  T part = 0;
   for (int e = tid; e < n2 * n2; e += nt) {
-    A[e] = T(Sh[e]);
+    T v = T(Sh[e]);
+    A[e] = v;
+    part += v * v;
     V[e] = (e % n2 == e / n2) ? T(1) : T(0);
+  }
+  const T fro2 = block_sum(part, red);
+  for (int j = wid; j < n2; j += nw) {
+    T s2 = 0;
+    for (int i = lane; i < n2; i += 32) s2 += A[j * n2 + i] * A[j * n2 + i];
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[j] = s2;
   }
   __syncthreads();
   const T eps = (sizeof(T) == 8) ? T(1e-14) : T(4e-6);
+  // columns below this squared norm are numerically null and are not rotated
+  const T null2 = fro2 * ((sizeof(T) == 8) ? T(1e-28) : T(1e-14));
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
@@ -179,19 +193,14 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
       for (int pi = wid; pi < n2 / 2; pi += nw) {
         int p, q;
         rr_pair(round, pi, n2, p, q);
+        const T al = nrm[p], be = nrm[q];
+        if (al <= null2 || be <= null2) continue;
         T* ap = A + p * n2;
         T* aq = A + q * n2;
-        T al = 0, be = 0, ga = 0;
-        for (int i = lane; i < n2; i += 32) {
-          T x = ap[i], y = aq[i];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        T ga = 0;
+        for (int i = lane; i < n2; i += 32) ga += ap[i] * aq[i];
         ga = warp_sum(ga);
-        if (ga != T(0) && fabs((double)ga) > (double)eps * sqrt((double)al * (double)be)) {
+        if (ga != T(0) && fabs(ga) > eps * sqrt(al * be)) {
           T zeta = (be - al) / (T(2) * ga);
           T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           T c = T(1) / sqrt(T(1) + t * t), s = c * t;
@@ -207,10 +216,23 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
             vp[i] = c * x - s * y;
             vq[i] = s * x + c * y;
           }
-          if (lane == 0) s_rot = 1;
+          __syncwarp();
+          if (lane == 0) {
+            // exact norms of the rotated pair: |a_p|^2 - t ga, |a_q|^2 + t ga
+            nrm[p] = al - t * ga;
+            nrm[q] = be + t * ga;
+            s_rot = 1;
+          }
         }
       }
       __syncthreads();
+    }
+    // refresh the norms from the columns once per sweep
+    for (int j = wid; j < n2; j += nw) {
+      T s2 = 0;
+      for (int i = lane; i < n2; i += 32) s2 += A[j * n2 + i] * A[j * n2 + i];
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[j] = s2;
     }
     __syncthreads();
     if (!s_rot) break;

@@ -213,8 +213,16 @@ def dlra_rank_log(ctx, beam_id: int, K: int):
     return log.reshape(K, 2)
 
 
+RANK_CAPS = (4, 8, 12, 16, 20, 24, 32, 40, 48, 64)
+
+
+def rank_capacity(rank_max: int) -> int:
+    """Column capacity the library allocates for a given rank_max."""
+    return next((c for c in RANK_CAPS if c >= rank_max), 64)
+
+
 def dlra_get_state(ctx, beam_id: int, n: int, m: int, rank_max: int):
-    RB = (rank_max + 3) // 4 * 4
+    RB = rank_capacity(rank_max)
     X = np.zeros(n * RB)
     S = np.zeros(RB * RB)
     W = np.zeros(m * RB)
@@ -232,7 +240,7 @@ def dlra_set_state(ctx, beam_id: int, X, S, W, rank_max: int):
     W = np.asarray(W, dtype=np.float64)
     S = np.asarray(S, dtype=np.float64)
     r = X.shape[1]
-    RB = (rank_max + 3) // 4 * 4
+    RB = rank_capacity(rank_max)
     Xc = np.ascontiguousarray(X.T).reshape(-1)
     Wc = np.ascontiguousarray(W.T).reshape(-1)
     Sc = np.zeros((RB, RB))
