@@ -178,10 +178,44 @@ dlra_status dlra_reset(dlra_ctx* ctx, int32_t retrace);
 dlra_status dlra_set_profiling(dlra_ctx* ctx, int32_t enable);
 dlra_status dlra_kernel_stats(dlra_ctx* ctx, double* total_ms, int64_t* launches);
 
+/* Arguments of the stand-alone streaming K-step (no context needed). All arrays are
+ * FP32 device memory of the current device, ordered with cuda_stream:
+ *   K0 (in), K1 (out) : n x r column-major, n = nx ny nz; K1 must not alias K0.
+ *   inv_rho           : n values 1/rho_s(x), where S(x, E) = rho_s(x) S_w(E).
+ *   P                 : nk matrices r x r, column-major, P_k at P + k r r, nk = 4 for an
+ *                       x-z slab (ny == 1, dy == 0) and 6 otherwise; k = 2 da + s pairs the
+ *                       stencil D^-_d (s = 0) with W^T A^+_d W and D^+_d (s = 1) with
+ *                       W^T A^-_d W, d running over the streaming directions x, (y,) z.
+ *   e0, de, n_sub     : energy at the start of the step, energy step, RK4 sub-steps.
+ *   bk_p, bk_alpha    : water stopping power S_w(E) = E^(1-p)/(p alpha).
+ * 1 <= r <= 64. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  int32_t r;
+  double e0, de;
+  int32_t n_sub;
+  double bk_p, bk_alpha;
+  const float* K0;
+  float* K1;
+  const float* inv_rho;
+  const float* P;
+  void* cuda_stream;
+} dlra_kstep_args;
+
+/* The K-step of the streaming update (Sec. 2.2, Eq. KLS first line, with F_S of
+ * Sec. 3.3.2 and RK4 time updates, Sec. 3.3.3): integrates
+ * K' = S_w(E(t))^-1 sum_k D_k(rho_s^-1 K) P_k from K(t_k) = K0 over one energy step
+ * with n_sub RK4 sub-steps, K1 = K(t_k + de). Allocates its work space (3 n x r
+ * and the packed P) with cudaMalloc and frees it before returning; synchronises
+ * cuda_stream. */
+dlra_status dlra_kstep(const dlra_kstep_args* args);
+
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);
 
-/* One-line description of the last error of this context (never NULL). */
+/* One-line description of the last error of this context (never NULL); with
+ * ctx == NULL, the last error of a context-free call on this host thread. */
 const char* dlra_last_error(const dlra_ctx* ctx);
 
 /* Release every resource of the context (NULL is ignored). */

@@ -125,6 +125,35 @@ __global__ void div_kernel(double* __restrict__ out, const double* __restrict__ 
 
 inline unsigned nblk(long long cnt, int bs) { return (unsigned)((cnt + bs - 1) / bs); }
 
+// Pst[(c*nk + k)*RB + c2] = P_k[c][c2] from column-major r x r blocks, zero padded
+__global__ void kstep_pack_p(const float* __restrict__ P, int r, int nk, int RB, float* __restrict__ Pst) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int tot = nk * RB * RB;
+  if (e >= tot) return;
+  int c2 = e % RB, row = e / RB;
+  int k = row % nk, c = row / nk;
+  Pst[e] = (c < r && c2 < r) ? P[(long long)k * r * r + (long long)c2 * r + c] : 0.f;
+}
+
+// y = K0 (zero columns beyond r), v = rho^-1 y
+__global__ void kstep_load(const float* __restrict__ K0, long long n, int r, int RB, const float* __restrict__ inv_rho,
+                           float* __restrict__ y, float* __restrict__ v) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * RB) return;
+  long long i = e % n;
+  int c = (int)(e / n);
+  float val = c < r ? K0[(long long)c * n + i] : 0.f;
+  y[e] = val;
+  v[e] = inv_rho[i] * val;
+}
+
+__global__ void kstep_store(const float* __restrict__ y, long long n, int r, float* __restrict__ K1) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * r) K1[e] = y[e];
+}
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
 // ---------------------------------------------------------------------------
 // launch helpers for the tiled product and the Gram reduction
 // ---------------------------------------------------------------------------
@@ -364,9 +393,10 @@ void moments_at(const dlra_ctx* c, int i, double E, std::vector<double>& self, s
   }
 }
 
-// Horner coefficients of one RK4 sub-step of y' = c(t) L y from pseudo-time t (energy Ea).
-void horner_betas(const dlra_ctx* c, double Ea, double hs, double* beta) {
-  const double c1 = 1.0 / Sw(c, Ea), c2 = 1.0 / Sw(c, Ea - 0.5 * hs), c4 = 1.0 / Sw(c, Ea - hs);
+// Horner coefficients of one RK4 sub-step of y' = c(t) L y, c = 1/S_w(E(t)), from energy Ea.
+void horner_betas_p(double bk_p, double bk_alpha, double Ea, double hs, double* beta) {
+  auto sw = [&](double E) { return std::pow(E, 1.0 - bk_p) / (bk_p * bk_alpha); };
+  const double c1 = 1.0 / sw(Ea), c2 = 1.0 / sw(Ea - 0.5 * hs), c4 = 1.0 / sw(Ea - hs);
   const double a1 = hs * (c1 + 4.0 * c2 + c4) / 6.0;
   const double a2 = hs * hs * (c1 * c2 + c2 * c2 + c2 * c4) / 6.0;
   const double a3 = hs * hs * hs * (c1 * c2 * c2 + c2 * c2 * c4) / 12.0;
@@ -375,6 +405,10 @@ void horner_betas(const dlra_ctx* c, double Ea, double hs, double* beta) {
   beta[1] = a3 / a2;
   beta[2] = a2 / a1;
   beta[3] = a1;
+}
+
+void horner_betas(const dlra_ctx* c, double Ea, double hs, double* beta) {
+  horner_betas_p(c->cfg.bk_p, c->cfg.bk_alpha, Ea, hs, beta);
 }
 
 // events around the streaming-stage kernel when profiling is on
@@ -1008,6 +1042,107 @@ void free_beams(dlra_ctx* ctx) {
 }  // namespace
 
 // ===========================================================================
+// stand-alone K-step on caller-provided work space
+// ===========================================================================
+namespace dlra {
+
+static int kstep_rank_cap(int r) {
+  for (int cap : kRankCaps)
+    if (cap >= r) return cap;
+  return -1;
+}
+
+size_t kstep_scratch_bytes(long long n, int r, int nact) {
+  const int RB = kstep_rank_cap(r);
+  if (RB < 0) return 0;
+  const size_t al = 256;
+  auto up = [&](size_t b) { return (b + al - 1) / al * al; };
+  return 3 * up(sizeof(float) * (size_t)n * RB) + up(sizeof(float) * (size_t)2 * nact * RB * RB) + up(sizeof(int));
+}
+
+int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, int msg_len) {
+  const dlra_kstep_args& a = *reinterpret_cast<const dlra_kstep_args*>(argp);
+  const bool two_d = a.ny == 1 && a.dy == 0.0;
+  const int nact = two_d ? 2 : 3;
+  const long long n = (long long)a.nx * a.ny * a.nz;
+  const int RB = kstep_rank_cap(a.r);
+  const size_t need = kstep_scratch_bytes(n, a.r, nact);
+  if (scratch_bytes < need) {
+    std::snprintf(msg, msg_len, "K-step needs %zu bytes of work space, %zu available", need, scratch_bytes);
+    return DLRA_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)a.cuda_stream;
+  const size_t al = 256;
+  auto up = [&](size_t b) { return (b + al - 1) / al * al; };
+  char* base = reinterpret_cast<char*>(scratch);
+  float* y = reinterpret_cast<float*>(base);
+  float* va = reinterpret_cast<float*>(base + up(sizeof(float) * (size_t)n * RB));
+  float* vb = reinterpret_cast<float*>(base + 2 * up(sizeof(float) * (size_t)n * RB));
+  float* Pst = reinterpret_cast<float*>(base + 3 * up(sizeof(float) * (size_t)n * RB));
+  int* rdev = reinterpret_cast<int*>(base + 3 * up(sizeof(float) * (size_t)n * RB) +
+                                     up(sizeof(float) * (size_t)2 * nact * RB * RB));
+  Geo g{};
+  g.nx = a.nx;
+  g.ny = a.ny;
+  g.nz = a.nz;
+  g.nxy = (long long)a.nx * a.ny;
+  g.n = n;
+  g.nact = nact;
+  if (two_d) { g.dirs[0] = 0; g.dirs[1] = 2; g.dirs[2] = 2; }
+  else { g.dirs[0] = 0; g.dirs[1] = 1; g.dirs[2] = 2; }
+  g.inv2d[0] = 1.0 / (2.0 * a.dx);
+  g.inv2d[1] = two_d ? 0.0 : 1.0 / (2.0 * a.dy);
+  g.inv2d[2] = 1.0 / (2.0 * a.dz);
+  const int nk = 2 * nact;
+  int64_t nl = 0;
+  set_int_kernel<<<1, 1, 0, st>>>(rdev, a.r);
+  kstep_pack_p<<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(a.P, a.r, nk, RB, Pst);
+  kstep_load<<<nblk(n * RB, 256), 256, 0, st>>>(a.K0, n, a.r, RB, a.inv_rho, y, va);
+  const double hs = a.de / a.n_sub;
+  for (int j = 0; j < a.n_sub; ++j) {
+    double beta[4];
+    horner_betas_p(a.bk_p, a.bk_alpha, a.e0 - j * hs, hs, beta);
+    const float* vins[4] = {va, vb, va, vb};
+    float* vouts[4] = {vb, va, vb, va};
+    for (int s2 = 0; s2 < 4; ++s2)
+      kstage<float>(RB, st, vins[s2], y, y, vouts[s2], n, a.inv_rho, g, Pst, rdev, (float)beta[s2], s2 == 3 ? 1 : 0,
+                    nl);
+  }
+  kstep_store<<<nblk(n * a.r, 256), 256, 0, st>>>(y, n, a.r, a.K1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(msg, msg_len, "K-step launch failed: %s", cudaGetErrorString(e));
+    return DLRA_ERR_CUDA;
+  }
+  return DLRA_OK;
+}
+
+static int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
+  if (!a) {
+    std::snprintf(msg, msg_len, "null arguments");
+    return DLRA_ERR_ARG;
+  }
+  const bool two_d = a->ny == 1 && a->dy == 0.0;
+  if (a->nx < 1 || a->ny < 1 || a->nz < 1 || !(a->dx > 0) || !(a->dz > 0) || !(two_d || a->dy > 0)) {
+    std::snprintf(msg, msg_len, "bad grid");
+    return DLRA_ERR_ARG;
+  }
+  if (a->r < 1 || a->r > 64 || a->n_sub < 1 || !(a->de > 0) || !(a->e0 - a->de > 0)) {
+    std::snprintf(msg, msg_len, "need 1 <= r <= 64, n_sub >= 1, e0 > de > 0");
+    return DLRA_ERR_ARG;
+  }
+  if (!a->K0 || !a->K1 || !a->inv_rho || !a->P || a->K0 == a->K1) {
+    std::snprintf(msg, msg_len, "null or aliased device arrays");
+    return DLRA_ERR_ARG;
+  }
+  return DLRA_OK;
+}
+
+}  // namespace dlra
+
+static thread_local char g_kstep_msg[256] = "no error";
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
@@ -1267,9 +1402,32 @@ dlra_status dlra_kernel_stats(dlra_ctx* ctx, double* total_ms, int64_t* launches
   return DLRA_OK;
 }
 
+dlra_status dlra_kstep(const dlra_kstep_args* args) {
+  int s = check_kstep_args(args, g_kstep_msg, sizeof g_kstep_msg);
+  if (s != DLRA_OK) return (dlra_status)s;
+  const bool two_d = args->ny == 1 && args->dy == 0.0;
+  const long long n = (long long)args->nx * args->ny * args->nz;
+  const size_t bytes = kstep_scratch_bytes(n, args->r, two_d ? 2 : 3);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    std::snprintf(g_kstep_msg, sizeof g_kstep_msg, "cudaMalloc of %zu bytes failed", bytes);
+    return DLRA_ERR_OOM;
+  }
+  s = run_kstep(args, scratch, bytes, g_kstep_msg, sizeof g_kstep_msg);
+  cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)args->cuda_stream);
+  cudaFree(scratch);
+  if (s == DLRA_OK && e2 != cudaSuccess) {
+    std::snprintf(g_kstep_msg, sizeof g_kstep_msg, "K-step failed: %s", cudaGetErrorString(e2));
+    s = DLRA_ERR_CUDA;
+  }
+  return (dlra_status)s;
+}
+
 int64_t dlra_launch_count(const dlra_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-const char* dlra_last_error(const dlra_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char* dlra_last_error(const dlra_ctx* ctx) { return ctx ? ctx->err.c_str() : g_kstep_msg; }
 
 void dlra_destroy(dlra_ctx* ctx) {
   if (!ctx) return;

@@ -76,4 +76,9 @@ struct RayGeo {
 void launch_raytrace(cudaStream_t st, const double* rays, int nray, RayGeo g, const double* f_cell,
                      const double* tau_cell, double* psi, double* e_u);
 
+// Work-space bytes of one stand-alone K-step (see dlra_kstep) and the step itself on
+// caller-provided device work space of at least that many bytes.
+size_t kstep_scratch_bytes(long long n, int r, int nact);
+int run_kstep(const void* args, void* scratch, size_t scratch_bytes, char* msg, int msg_len);
+
 }  // namespace dlra

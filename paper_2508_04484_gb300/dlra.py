@@ -52,6 +52,15 @@ class dlra_beam(C.Structure):
                 ("dir", C.c_double * 3), ("spot_sigma", C.c_double), ("weight", C.c_double)]
 
 
+class dlra_kstep_args(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("r", C.c_int32), ("e0", C.c_double), ("de", C.c_double), ("n_sub", C.c_int32),
+                ("bk_p", C.c_double), ("bk_alpha", C.c_double),
+                ("K0", C.c_void_p), ("K1", C.c_void_p), ("inv_rho", C.c_void_p), ("P", C.c_void_p),
+                ("cuda_stream", C.c_void_p)]
+
+
 # names, argument types and return type of every entry point of include/dlra.h
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -72,6 +81,7 @@ SIGNATURES = {
     "dlra_reset": ([_P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
+    "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_launch_count": ([_P], C.c_int64),
     "dlra_last_error": ([_P], C.c_char_p),
     "dlra_destroy": ([_P], None),
@@ -282,6 +292,27 @@ def dlra_kernel_stats(ctx):
     cnt = C.c_int64()
     _check(ctx, load().dlra_kernel_stats(ctx, C.byref(ms), C.byref(cnt)))
     return ms.value, cnt.value
+
+
+def kstep_args(grid: dict, r: int, e0: float, de: float, n_sub: int, K0, K1, inv_rho, P, stream=None,
+               bk_p=1.77, bk_alpha=0.0022):
+    """Argument block of dlra_kstep for torch CUDA float32 tensors K0, K1 (n x r
+    column-major, i.e. shape (r, n)), inv_rho (n) and P (nk, r, r) with P_k
+    column-major (pass the transposes of the row-major r x r matrices)."""
+    a = dlra_kstep_args()
+    a.nx, a.ny, a.nz = int(grid["nx"]), int(grid["ny"]), int(grid["nz"])
+    a.dx, a.dy, a.dz = float(grid["dx"]), float(grid["dy"]), float(grid["dz"])
+    a.r, a.e0, a.de, a.n_sub = int(r), float(e0), float(de), int(n_sub)
+    a.bk_p, a.bk_alpha = float(bk_p), float(bk_alpha)
+    a.K0, a.K1, a.inv_rho, a.P = K0.data_ptr(), K1.data_ptr(), inv_rho.data_ptr(), P.data_ptr()
+    a.cuda_stream = stream
+    return a
+
+
+def dlra_kstep(args):
+    st = load().dlra_kstep(C.byref(args))
+    if st != DLRA_OK:
+        raise DlraError(st, load().dlra_last_error(None).decode())
 
 
 def dlra_launch_count(ctx) -> int:
