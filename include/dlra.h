@@ -211,6 +211,20 @@ typedef struct {
  * cuda_stream. */
 dlra_status dlra_kstep(const dlra_kstep_args* args);
 
+/* The same K-step as dlra_kstep for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is a library-usage variant). Its work space
+ * is a static device array of 32 MiB held by every GPU that loads the library
+ * until the process exits; problems whose work space (3 n rcap + 6 rcap^2 FP32
+ * words, rcap = r rounded up to 4, 8, ..., 24, 32, 40, 48 or 64) exceeds it are
+ * rejected with DLRA_ERR_ARG and a message naming both sizes. The first call on
+ * each device looks up the array's device address with that device current; make
+ * that first call before any stream capture. Every call uses the whole array and
+ * writes all of it that it reads (nothing needs to start at zero); calls that
+ * overlap on the GPU (different streams, threads or processes sharing a context)
+ * race on it. Enqueued on cuda_stream without synchronising; calls no cudaMalloc
+ * or cudaFree. */
+dlra_status dlra_kstep_noalloc(const dlra_kstep_args* args);
+
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);
 

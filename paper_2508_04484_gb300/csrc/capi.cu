@@ -1117,7 +1117,7 @@ int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, 
   return DLRA_OK;
 }
 
-static int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
+int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
   if (!a) {
     std::snprintf(msg, msg_len, "null arguments");
     return DLRA_ERR_ARG;
@@ -1141,6 +1141,11 @@ static int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
 }  // namespace dlra
 
 static thread_local char g_kstep_msg[256] = "no error";
+
+namespace dlra {
+// message returned by dlra_last_error(NULL) after a failed context-free call
+void set_context_free_error(const char* msg) { std::snprintf(g_kstep_msg, sizeof g_kstep_msg, "%s", msg); }
+}  // namespace dlra
 
 // ===========================================================================
 // C ABI

@@ -82,6 +82,7 @@ SIGNATURES = {
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
+    "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_launch_count": ([_P], C.c_int64),
     "dlra_last_error": ([_P], C.c_char_p),
     "dlra_destroy": ([_P], None),
@@ -311,6 +312,13 @@ def kstep_args(grid: dict, r: int, e0: float, de: float, n_sub: int, K0, K1, inv
 
 def dlra_kstep(args):
     st = load().dlra_kstep(C.byref(args))
+    if st != DLRA_OK:
+        raise DlraError(st, load().dlra_last_error(None).decode())
+
+
+def dlra_kstep_noalloc(args):
+    """dlra_kstep on the library's static work space (no device allocation)."""
+    st = load().dlra_kstep_noalloc(C.byref(args))
     if st != DLRA_OK:
         raise DlraError(st, load().dlra_last_error(None).decode())
 
