@@ -318,6 +318,9 @@ struct dlra_ctx {
   // ray sets of the beams (for dlra_reset with retrace)
   std::vector<double*> ray_dev;
   std::vector<int> ray_count;
+  // internal stream for the moment-side (m) work that overlaps the cell-side work
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // streaming-stage kernel timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -506,39 +509,59 @@ struct Engine {
                 nl);
   }
 
+  // fork: st2 waits for everything enqueued so far on st
+  void fork() {
+    cudaEventRecord(ctx->ev[0], ctx->st);
+    cudaStreamWaitEvent(ctx->st2, ctx->ev[0], 0);
+  }
+  // st waits for everything enqueued so far on st2
+  void join() {
+    cudaEventRecord(ctx->ev[3], ctx->st2);
+    cudaStreamWaitEvent(ctx->st, ctx->ev[3], 0);
+  }
+
   void streaming(Beam<T>& B, int k) {
     const long long n = ctx->n;
     const int RB = ctx->RB, m = ctx->m, nk = ctx->nk, n2 = ctx->n2;
-    cudaStream_t st = ctx->st;
+    cudaStream_t st = ctx->st;     // cell-side chain
+    cudaStream_t sm = ctx->st2;    // moment-side chain
     int64_t& nl = ctx->launches;
     const int* rdim = &B.dims->r;
     T* Zm = P(ctx->Zm);
-    // P_k = W^T A^s_d W
-    gemm<T, 16>(st, (long long)nk * m, RB, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
+    fork();
+    // [m] P_k = W^T A^s_d W, packed for the stage kernel; L0 = W S^T
+    gemm<T, 16>(sm, (long long)nk * m, RB, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{B.W, m, nullptr, m, rdim, RB}, EpiStoreKBlocks<T>{Zm, m, RB}, nl);
-    cudaMemsetAsync(ctx->P1, 0, sizeof(double) * nk * RB * RB, st);
-    gram<T>(st, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, ctx->P1, RB, nl);
-    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->P1, RB, nk, P(ctx->Pst));
+    cudaMemsetAsync(ctx->P1, 0, sizeof(double) * nk * RB * RB, sm);
+    gram<T>(sm, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, ctx->P1, RB, nl);
+    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, sm>>>(ctx->P1, RB, nk, P(ctx->Pst));
     ++nl;
-    // G_k = X^T D_k rho^-1 X
+    cudaEventRecord(ctx->ev[1], sm);
+    T* ly = P(ctx->Lb[0]);
+    T* la = P(ctx->Lb[1]);
+    T* lb = P(ctx->Lb[2]);
+    gemm<T, 16>(sm, m, RB, RB, ALoadPlain<T>{B.W, m, rdim, RB}, BLoadRow<T, double>{B.S, RB, RB, RB},
+                EpiStore<T>{ly, m, nullptr, m, T(1), T(0)}, nl);
+    // [n] G_k = X^T D_k rho^-1 X; K0 = X S (and rho^-1 K0)
     cudaMemsetAsync(ctx->G1, 0, sizeof(double) * nk * RB * RB, st);
     gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, ctx->G1, RB, RB, nl);
     gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->G1, RB, nk, P(ctx->GtT));
     ++nl;
-    // K-step: K0 = X S (and rho^-1 K0), RK4 Horner stages z <- y + beta L(z) on scaled inputs
+    cudaEventRecord(ctx->ev[2], st);
     T* y = P(ctx->Kb[0]);
     T* va = P(ctx->Kb[1]);
     T* vb = P(ctx->Kb[2]);
     gemm<T, 16>(st, n, RB, RB, ALoadPlain<T>{B.X, n, rdim, RB}, BLoadCol<T, double>{B.S, RB, nullptr, RB, nullptr, RB},
                 EpiStoreScaled<T>{y, va, n, P(ctx->inv_rho)}, nl);
-    // L-step: L0 = W S^T
-    T* ly = P(ctx->Lb[0]);
-    T* la = P(ctx->Lb[1]);
-    T* lb = P(ctx->Lb[2]);
-    gemm<T, 16>(st, m, RB, RB, ALoadPlain<T>{B.W, m, rdim, RB}, BLoadRow<T, double>{B.S, RB, RB, RB},
-                EpiStore<T>{ly, m, nullptr, m, T(1), T(0)}, nl);
+    cudaStreamWaitEvent(st, ctx->ev[1], 0);   // stage kernel needs P
+    cudaStreamWaitEvent(sm, ctx->ev[2], 0);   // L-stage needs G
+    // RK4 Horner stages: K-step on st, L-step on sm
     const int ns = ctx->nsub[k];
     const double hs = ctx->h / ns;
+    const size_t lsmem =
+        ((size_t)nk * m + (size_t)nk * RB * RB + (size_t)(128 / (RB <= 32 ? 32 : 64)) * nk * RB) * sizeof(T);
+    if (lsmem > 48 * 1024)
+      cudaFuncSetAttribute(lstage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
     for (int j = 0; j < ns; ++j) {
       double beta[4];
       horner_betas(ctx, ctx->E[k] - j * hs, hs, beta);
@@ -546,36 +569,30 @@ struct Engine {
       T* vouts[4] = {vb, va, vb, va};
       const T* lin = ly;
       T* louts[4] = {la, lb, la, ly};
-      for (int s = 0; s < 4; ++s) {
+      for (int s2 = 0; s2 < 4; ++s2) {
         prof_begin(ctx);
-        kstage<T>(RB, st, vins[s], y, y, vouts[s], n, P(ctx->inv_rho), ctx->geo, P(ctx->Pst), rdim, T(beta[s]),
-                  s == 3 ? 1 : 0, nl);
+        kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(ctx->Pst), rdim,
+                  T(beta[s2]), s2 == 3 ? 1 : 0, nl);
         prof_end(ctx);
-        // m-side: out = y + beta sum_k A^s_d z G_k^T
-        {
-          const size_t smem = ((size_t)nk * m + (size_t)nk * RB * RB + (size_t)(128 / (RB <= 32 ? 32 : 64)) * nk * RB) * sizeof(T);
-          if (smem > 48 * 1024)
-            cudaFuncSetAttribute(lstage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-          lstage_kernel<T><<<m, 128, smem, st>>>(P(ctx->Apm), m, nk, lin, ly, louts[s], P(ctx->GtT), RB, rdim,
-                                                T(beta[s]));
-          ++nl;
-        }
-        lin = louts[s];
+        lstage_kernel<T><<<m, 128, lsmem, sm>>>(P(ctx->Apm), m, nk, lin, ly, louts[s2], P(ctx->GtT), RB, rdim,
+                                                 T(beta[s2]));
+        ++nl;
+        lin = louts[s2];
       }
     }
-    // augmentation of both bases
+    // augmentation of both bases, then the Galerkin operators on them
     augment_x(B, y, RB);
-    launch_waug<T, T>(st, B.W, m, RB, ly, m, RB, drop1(), P(ctx->Wh), B.dims);
+    launch_waug<T, T>(sm, B.W, m, RB, ly, m, RB, drop1(), P(ctx->Wh), B.dims);
     ++nl;
-    // Galerkin operators on the augmented bases
     T* Xh = P(ctx->Xh);
     T* Wh = P(ctx->Wh);
     cudaMemsetAsync(ctx->Gc, 0, sizeof(double) * nk * n2 * n2, st);
     gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, ctx->Gc, n2, n2, nl);
-    gemm<T, 16>(st, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
+    gemm<T, 16>(sm, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{Wh, m, nullptr, m, nullptr, n2}, EpiStoreKBlocks<T>{Zm, m, n2}, nl);
-    cudaMemsetAsync(ctx->Ph, 0, sizeof(double) * nk * n2 * n2, st);
-    gram<T>(st, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, ctx->Ph, n2, nl);
+    cudaMemsetAsync(ctx->Ph, 0, sizeof(double) * nk * n2 * n2, sm);
+    gram<T>(sm, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, ctx->Ph, n2, nl);
+    join();
     launch_sstep<T>(st, ctx->Gc, ctx->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, ctx->Sh);
     ++nl;
     launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 0, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
@@ -605,14 +622,16 @@ struct Engine {
     cudaStream_t st = ctx->st;
     int64_t& nl = ctx->launches;
     T* A = P(ctx->Asrc);
+    const double* Bk = B.Bsrc + (long long)k * M * m;
+    fork();
+    launch_waug<T, double>(ctx->st2, B.W, m, RB, Bk, m, M, drop1(), P(ctx->Wh), B.dims);
+    ++nl;
     src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), B.psi + (long long)k * n, n, M, A);
     ++nl;
     augment_x(B, A, M);
-    const double* Bk = B.Bsrc + (long long)k * M * m;
-    launch_waug<T, double>(st, B.W, m, RB, Bk, m, M, drop1(), P(ctx->Wh), B.dims);
-    ++nl;
     cudaMemsetAsync(ctx->XA, 0, sizeof(double) * n2 * M, st);
     gram<T>(st, n, P(ctx->Xh), n, nullptr, n2, M, FPlain<T>{A, n, nullptr, M}, ctx->XA, n2, nl);
+    join();
     launch_src_assemble<T>(st, B.S, RB, ctx->XA, Bk, P(ctx->Wh), m, M, n2, ctx->h, ctx->Sh);
     ++nl;
     launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 1, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
@@ -1236,6 +1255,8 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
     *out = c.release();
     return s;
   }
+  CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
+  for (int i = 0; i < 4; ++i) CK(cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming));
   if (!ctx->schedule_host.empty()) {
     ALLOC(ctx->schedule_dev, sizeof(int) * ctx->schedule_host.size());
     CK(cudaMemcpy(ctx->schedule_dev, ctx->schedule_host.data(), sizeof(int) * ctx->schedule_host.size(),
@@ -1437,7 +1458,11 @@ const char* dlra_last_error(const dlra_ctx* ctx) { return ctx ? ctx->err.c_str()
 void dlra_destroy(dlra_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
+  if (ctx->st2) cudaStreamSynchronize(ctx->st2);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->st2) cudaStreamDestroy(ctx->st2);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->beams) {
     if (ctx->fp64) free_beams<double>(ctx);
