@@ -177,12 +177,17 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
   const int tile = area32 < area64 ? 32 : 64;
   int gy = (acap + tile - 1) / tile, gz = (ncols_j + tile - 1) / tile;
   long long want = (rows + GR_TC - 1) / GR_TC;
-  long long cap = std::max(1, (tile == 64 ? 1216 : 2432) / (gy * gz));
-  int gx = (int)std::max(1LL, std::min(want, cap));
-  if (tile == 64)
-    gram_kernel<T, F, 64><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
-  else
-    gram_kernel<T, F, 32><<<dim3(gx, gy, gz), 64, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  if (tile == 64) {
+    long long cap = std::max(1, 1216 / (gy * gz));
+    int gx = (int)std::max(1LL, std::min(want, cap));
+    gram_kernel<T, F, 64, 1><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  } else {
+    // row groups per block: 4 (FP32) / 2 (FP64) keep the static staging below 48 KB
+    constexpr int RG = sizeof(T) == 4 ? 4 : 2;
+    long long cap = std::max(1, 1216 / (gy * gz));
+    int gx = (int)std::max(1LL, std::min((want + RG - 1) / RG, cap));
+    gram_kernel<T, F, 32, RG><<<dim3(gx, gy, gz), 64 * RG, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
+  }
   ++nl;
 }
 
@@ -246,6 +251,35 @@ void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, in
   const int gx = (int)std::max(1LL, std::min(chunks, (long long)std::max(1, 152 * per_sm / nslice)));
   kern<<<dim3(gx, nslice), threads, smem, st>>>(rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, jslice, out,
                                                 ldj, ldo);
+  ++nl;
+}
+
+template <typename T, int NM>
+void apply_launch(cudaStream_t st, long long rows, const T* A, long long lda, int Q, const int* qdim, const double* M,
+                  long long ldm, int N, T* C, long long ldc, const T* Cin, T alpha, T beta, T* V, const T* inv_rho) {
+  const size_t smem = (size_t)Q * NM * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(apply_kernel<T, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  apply_kernel<T, NM><<<nblk(rows, 128), 128, smem, st>>>(rows, A, lda, Q, qdim, M, ldm, N, C, ldc, Cin, alpha, beta,
+                                                          V, inv_rho);
+}
+
+// C(:, :N) = alpha A(:, :Q) M + beta Cin (+ V = rho^-1 C); N <= 64
+template <typename T>
+void apply(cudaStream_t st, long long rows, const T* A, long long lda, int Q, const int* qdim, const double* M,
+           long long ldm, int N, T* C, long long ldc, const T* Cin, T alpha, T beta, int64_t& nl, T* V = nullptr,
+           const T* inv_rho = nullptr) {
+  if (rows <= 0 || N <= 0) return;
+  const int nm = N <= 4 ? 4 : N <= 8 ? 8 : N <= 12 ? 12 : N <= 16 ? 16 : N <= 20 ? 20 : N <= 24 ? 24
+               : N <= 32 ? 32 : N <= 40 ? 40 : N <= 48 ? 48 : 64;
+  switch (nm) {
+#define AP_CASE(R) \
+  case R: apply_launch<T, R>(st, rows, A, lda, Q, qdim, M, ldm, N, C, ldc, Cin, alpha, beta, V, inv_rho); break;
+    AP_CASE(4) AP_CASE(8) AP_CASE(12) AP_CASE(16) AP_CASE(20) AP_CASE(24) AP_CASE(32) AP_CASE(40) AP_CASE(48)
+    AP_CASE(64)
+#undef AP_CASE
+    default: break;
+  }
   ++nl;
 }
 
@@ -480,9 +514,7 @@ struct Engine {
     cudaMemsetAsync(ctx->C1, 0, sizeof(double) * RB * qcap, st);
     gram<T>(st, n, B.X, n, rdim, RB, qcap, FPlain<T>{K, n, nullptr, qcap}, ctx->C1, RB, nl);
     // R = K - X C1 into X^[:, RB:RB+qcap]
-    gemm<T, 16>(st, n, qcap, RB, ALoadPlain<T>{B.X, n, rdim, RB},
-                BLoadCol<T, double>{ctx->C1, RB, nullptr, RB, nullptr, qcap},
-                EpiStore<T>{Xh + (long long)RB * n, n, K, n, T(-1), T(1)}, nl);
+    apply<T>(st, n, B.X, n, RB, rdim, ctx->C1, RB, qcap, Xh + (long long)RB * n, n, K, T(-1), T(1), nl);
     for (int pass = 0; pass < 2; ++pass) {
       const int lg = RB + qcap;
       cudaMemsetAsync(ctx->Cg, 0, sizeof(double) * lg * qcap, st);
@@ -490,9 +522,7 @@ struct Engine {
       launch_orth_factor(st, ctx->Cg, pass == 0 ? ctx->C1 : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
                          ctx->Mapply, &B.dims->qx, ctx->dev_err);
       ++nl;
-      gemm<T, 16>(st, n, qcap, lg, ALoadPlain<T>{Xh, n, nullptr, lg},
-                  BLoadCol<T, double>{ctx->Mapply, lg, nullptr, lg, nullptr, qcap},
-                  EpiStore<T>{Xh + (long long)RB * n, n, nullptr, n, T(1), T(0)}, nl);
+      apply<T>(st, n, Xh, n, lg, nullptr, ctx->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl);
     }
   }
 
@@ -501,9 +531,7 @@ struct Engine {
     const long long n = ctx->n;
     const int RB = ctx->RB, n2 = ctx->n2, m = ctx->m;
     int64_t& nl = ctx->launches;
-    gemm<T, 16>(ctx->st, n, RB, n2, ALoadPlain<T>{P(ctx->Xh), n, nullptr, n2},
-                BLoadCol<T, double>{ctx->Pt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.X, n, nullptr, n, T(1), T(0)},
-                nl);
+    apply<T>(ctx->st, n, P(ctx->Xh), n, n2, nullptr, ctx->Pt, n2, RB, B.X, n, nullptr, T(1), T(0), nl);
     gemm<T, 16>(ctx->st, m, RB, n2, ALoadPlain<T>{P(ctx->Wh), m, nullptr, n2},
                 BLoadCol<T, double>{ctx->Qt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.W, m, nullptr, m, T(1), T(0)},
                 nl);
@@ -551,8 +579,7 @@ struct Engine {
     T* y = P(ctx->Kb[0]);
     T* va = P(ctx->Kb[1]);
     T* vb = P(ctx->Kb[2]);
-    gemm<T, 16>(st, n, RB, RB, ALoadPlain<T>{B.X, n, rdim, RB}, BLoadCol<T, double>{B.S, RB, nullptr, RB, nullptr, RB},
-                EpiStoreScaled<T>{y, va, n, P(ctx->inv_rho)}, nl);
+    apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho));
     cudaStreamWaitEvent(st, ctx->ev[1], 0);   // stage kernel needs P
     cudaStreamWaitEvent(sm, ctx->ev[2], 0);   // L-stage needs G
     // RK4 Horner stages: K-step on st, L-step on sm

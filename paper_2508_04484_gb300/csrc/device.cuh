@@ -60,8 +60,8 @@ __device__ __forceinline__ void cell_coords(long long i, const Geo& g, int& ix, 
 // the ghost layers are zero without branches).
 template <typename T, int TT>
 __device__ void stencil_tables(int* sOff, T* sR, long long row0, long long rows, const T* __restrict__ inv_rho,
-                               const Geo& g) {
-  for (int e = threadIdx.x; e < 13 * TT; e += blockDim.x) {
+                               const Geo& g, int tid, int nt) {
+  for (int e = tid; e < 13 * TT; e += nt) {
     const int pt = e / TT, t = e % TT;
     const long long r = row0 + t;
     int off = 0;
@@ -159,7 +159,7 @@ struct ALoadStencil {
   __device__ void init(void* ex, long long row0, long long rows) const {
     int* sOff = reinterpret_cast<int*>(ex);
     T* sR = reinterpret_cast<T*>(sOff + 13 * GM_BM);
-    stencil_tables<T, GM_BM>(sOff, sR, row0, rows, inv_rho, g);
+    stencil_tables<T, GM_BM>(sOff, sR, row0, rows, inv_rho, g, threadIdx.x, blockDim.x);
   }
   __device__ void load(T* sA, int BK, int q0, long long row0, long long rows, const void* ex) const {
     const int* sOff = reinterpret_cast<const int*>(ex);
@@ -481,6 +481,59 @@ struct EpiStoreScaled {  // C = acc and V = rho^-1 acc
 };
 
 // ---------------------------------------------------------------------------
+// Tall-skinny apply, one thread per row with the NM outputs in registers:
+//   C(i, c) = alpha sum_q A(i, q) M(q, c) + beta Cin(i, c)   (c < NM, q < Q)
+// A column-major (lda), M FP64 column-major (ldm) staged in shared memory as T;
+// mode 1 also writes V(i, c) = inv_rho(i) C(i, c).
+// ---------------------------------------------------------------------------
+template <typename T, int NM>
+__global__ void __launch_bounds__(128) apply_kernel(long long rows, const T* __restrict__ A, long long lda, int Q,
+                                                    const int* __restrict__ qdim, const double* __restrict__ M,
+                                                    long long ldm, int N, T* __restrict__ C, long long ldc,
+                                                    const T* __restrict__ Cin, T alpha, T beta, T* __restrict__ V,
+                                                    const T* __restrict__ inv_rho) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* sM = reinterpret_cast<T*>(raw);  // Q x NM, row q contiguous
+  const int Qa = dev_dim(qdim, Q);
+  for (int e = threadIdx.x; e < Qa * NM; e += blockDim.x) {
+    const int q = e / NM, c = e - q * NM;
+    sM[e] = c < N ? T(M[(long long)c * ldm + q]) : T(0);
+  }
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  T acc[NM];
+#pragma unroll
+  for (int c = 0; c < NM; ++c) acc[c] = T(0);
+  const T* a = A + i;
+  T cur = Qa > 0 ? a[0] : T(0);
+  for (int q = 0; q < Qa; ++q) {
+    const T nxt = q + 1 < Qa ? a[(long long)(q + 1) * lda] : T(0);
+    const T* mrow = sM + q * NM;
+#pragma unroll
+    for (int c = 0; c < NM; c += 4) {
+      T m4[4];
+      Vec4<T>::load(mrow + c, m4);
+      acc[c] += cur * m4[0];
+      acc[c + 1] += cur * m4[1];
+      acc[c + 2] += cur * m4[2];
+      acc[c + 3] += cur * m4[3];
+    }
+    cur = nxt;
+  }
+  const T ir = V ? inv_rho[i] : T(0);
+#pragma unroll
+  for (int c = 0; c < NM; ++c) {
+    if (c < N) {
+      T v = alpha * acc[c];
+      if (Cin) v += beta * Cin[(long long)c * ldc + i];
+      C[(long long)c * ldc + i] = v;
+      if (V) V[(long long)c * ldc + i] = ir * v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Stencil Gram G_k[a][b] = sum_i A(i, a) D_k(rho^-1 B(:, b))(i), k = 2 da + s,
 // written at out[(k * ldj + b) * ldo + a]. A block takes a 64-cell chunk at a time,
 // stages A and the nk stencil values of every B column in shared memory (13 loads
@@ -519,7 +572,7 @@ __global__ void __launch_bounds__(512) gram_stencil_kernel(long long rows, const
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = T(0);
   for (long long r0 = (long long)blockIdx.x * GS_TC; r0 < rows; r0 += (long long)gridDim.x * GS_TC) {
-    stencil_tables<T, GS_TC>(sOff, sR, r0, rows, inv_rho, g);
+    stencil_tables<T, GS_TC>(sOff, sR, r0, rows, inv_rho, g, threadIdx.x, blockDim.x);
     for (int e = tid; e < GS_TC * naP; e += blockDim.x) {
       int t = e % GS_TC, a = e / GS_TC;
       long long rr = r0 + t;
@@ -646,7 +699,7 @@ __global__ void __launch_bounds__(128) lstage_kernel(const T* __restrict__ Apm, 
 template <typename T>
 struct FPlain {  // F(row, j) = B[j * ldb + row], zero for j >= jdim
   static constexpr bool kTables = false;
-  __device__ void prep(int*, T*, long long, long long) const {}
+  __device__ void prep(int*, T*, long long, long long, int, int) const {}
   const T* B;
   long long ldb;
   const int* jdim;
@@ -660,7 +713,7 @@ struct FPlain {  // F(row, j) = B[j * ldb + row], zero for j >= jdim
 template <typename T>
 struct FDiag {  // F(row, k * nb + b) = wv[k * n + row] * B[b * ldb + row]
   static constexpr bool kTables = false;
-  __device__ void prep(int*, T*, long long, long long) const {}
+  __device__ void prep(int*, T*, long long, long long, int, int) const {}
   const T* B;
   long long ldb;
   const T* wv;
@@ -686,8 +739,8 @@ struct FStencil {  // F(row, k * nb + b) = D_k(rho^-1 B[:, b])(row), tables per 
   Geo g;
   int nb;
   const int* bdim;
-  __device__ void prep(int* sOff, T* sR, long long r0, long long rows) const {
-    stencil_tables<T, GR_TC>(sOff, sR, r0, rows, inv_rho, g);
+  __device__ void prep(int* sOff, T* sR, long long r0, long long rows, int tid, int nt) const {
+    stencil_tables<T, GR_TC>(sOff, sR, r0, rows, inv_rho, g, tid, nt);
   }
   __device__ T operator()(long long r, int j, int bact, int t, const int* sOff, const T* sR) const {
     int k = j / nb, b = j - k * nb;
@@ -707,66 +760,78 @@ struct FStencil {  // F(row, k * nb + b) = D_k(rho^-1 B[:, b])(row), tables per 
 
 
 
-template <typename T, class F, int TILE>
+template <typename T, class F, int TILE, int RG>
 __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __restrict__ A, long long lda,
                                                    const int* adim, int acap, int ncols_j, F f,
                                                    double* __restrict__ out, long long ldo) {
+  // RG row groups per block, each with its own 32-row chunks and staging buffers;
+  // their partial tiles are summed in shared memory before the FP64 atomics.
   constexpr int TPD = TILE / 4;  // threads per tile dimension, 4 x 4 outputs each
-  __shared__ T sA[GR_TC][TILE + 1];
-  __shared__ T sF[GR_TC][TILE + 1];
-  __shared__ int sOff[F::kTables ? 13 * GR_TC : 1];
-  __shared__ T sR[F::kTables ? 13 * GR_TC : 1];
-  const int tid = threadIdx.x;
+  constexpr int GT = TPD * TPD;  // threads per row group
+  __shared__ T sA[RG][GR_TC][TILE + 1];
+  __shared__ T sF[RG][GR_TC][TILE + 1];
+  __shared__ int sOff[F::kTables ? RG * 13 * GR_TC : 1];
+  __shared__ T sR[F::kTables ? RG * 13 * GR_TC : 1];
+  const int g = threadIdx.x / GT, tid = threadIdx.x % GT;
   const int ta = tid % TPD, tj = tid / TPD;
   const int a0 = blockIdx.y * TILE, j0 = blockIdx.z * TILE;
   const int Aact = dev_dim(adim, acap);
   const int Jact = f.jact();
-  T acc[4][4], cmp[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); cmp[i][j] = T(0); }
-  for (long long r0 = (long long)blockIdx.x * GR_TC; r0 < rows; r0 += (long long)gridDim.x * GR_TC) {
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const long long stride = (long long)gridDim.x * RG * GR_TC;
+  const long long nchunk_iter = (rows + stride - 1) / stride;
+  for (long long it = 0; it < nchunk_iter; ++it) {
+    const long long r0 = it * stride + ((long long)blockIdx.x * RG + g) * GR_TC;
     if (F::kTables) {
-      f.prep(sOff, sR, r0, rows);
+      f.prep(sOff + g * 13 * GR_TC, sR + g * 13 * GR_TC, r0, rows, tid, GT);
       __syncthreads();
     }
-    for (int e = tid; e < GR_TC * TILE; e += blockDim.x) {
+    for (int e = tid; e < GR_TC * TILE; e += GT) {
       int t = e % GR_TC, c = e / GR_TC;
       long long r = r0 + t;
       int a = a0 + c, j = j0 + c;
-      sA[t][c] = (r < rows && a < Aact && a < acap) ? A[(long long)a * lda + r] : T(0);
-      sF[t][c] = (r < rows && j < ncols_j) ? f(r, j, Jact, t, sOff, sR) : T(0);
+      sA[g][t][c] = (r < rows && a < Aact && a < acap) ? A[(long long)a * lda + r] : T(0);
+      sF[g][t][c] = (r < rows && j < ncols_j) ? f(r, j, Jact, t, sOff + g * 13 * GR_TC, sR + g * 13 * GR_TC) : T(0);
     }
     __syncthreads();
-    T p[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) p[i][j] = T(0);
 #pragma unroll 8
     for (int t = 0; t < GR_TC; ++t) {
       T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[t][ta + TPD * i];
+      for (int i = 0; i < 4; ++i) a[i] = sA[g][t][ta + TPD * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sF[t][tj + TPD * j];
+      for (int j = 0; j < 4; ++j) b[j] = sF[g][t][tj + TPD * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) p[i][j] += a[i] * b[j];
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
     }
-    // compensated accumulation of the chunk partials
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        T y = p[i][j] - cmp[i][j];
-        T s = acc[i][j] + y;
-        cmp[i][j] = (s - acc[i][j]) - y;
-        acc[i][j] = s;
-      }
     __syncthreads();
+  }
+  // sum the row groups' tiles through shared memory (reusing sA)
+  if (RG > 1) {
+    T* red = &sA[0][0][0];
+    for (int gg = 1; gg < RG; ++gg) {
+      if (g == gg) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) red[(i * 4 + j) * GT + tid] = acc[i][j];
+      }
+      __syncthreads();
+      if (g == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += red[(i * 4 + j) * GT + tid];
+      }
+      __syncthreads();
+    }
+    if (g != 0) return;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -776,7 +841,7 @@ __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __re
     for (int j = 0; j < 4; ++j) {
       int jj = j0 + tj + TPD * j;
       if (jj >= ncols_j) continue;
-      double v = (double)acc[i][j] - (double)cmp[i][j];
+      double v = (double)acc[i][j];
       if (v != 0.0) atomicAdd(out + (long long)jj * ldo + a, v);
     }
   }
