@@ -45,12 +45,14 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--energy-steps", type=int, default=0,
                    help="profiling only: stop each solve after this many energy steps")
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=[WORKLOAD, "phantom_48cube_8beams", "phantom_96cube_32beams", "phantom_128cube_adaptive"])
     return p.parse_args()
 
 
-def _workload():
+def _workload(name=WORKLOAD):
     from paper_2508_04484_gb300 import workloads as WL
-    return WL.water_64cube_boltzmann()
+    return getattr(WL, name)()
 
 
 def _stage_traffic():
@@ -174,6 +176,40 @@ def cpu_baseline(cfg, mats, w, beams, budget_steps=4):
                       f"{dt:.1f} s, numpy/BLAS threads on {cores} cores"}
 
 
+def _solve_ms(cfg, mats, w, beams, K, lanes, reps):
+    """Mean device time (ms) of one whole solve with the given number of lanes."""
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    stream = torch.cuda.Stream()
+    s = D.Solver(dict(cfg, max_concurrent_beams=lanes), mats, w, beams, stream=stream.cuda_stream)
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    dose = torch.zeros(n, dtype=torch.float64, device="cuda")
+    times = []
+    for i in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.reset(retrace=True)
+        s.step(K)
+        s.dose(out=dose)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            times.append(e0.elapsed_time(e1))
+    s.close()
+    return float(np.mean(times))
+
+
+def _plain_vs_batched(cfg, mats, w, beams, K, args):
+    """The same multi-beam solve with one beam after the other (one lane) and with the
+    beams advanced concurrently (one lane per beam)."""
+    reps = max(1, min(args.steps, 3))
+    plain = _solve_ms(cfg, mats, w, beams, K, 1, reps)
+    batched = _solve_ms(cfg, mats, w, beams, K, min(len(beams), 32), reps)
+    return {"plain_ms_per_solve": plain, "batched_ms_per_solve": batched, "speedup": plain / batched,
+            "beams": len(beams), "lanes": min(len(beams), 32)}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -215,11 +251,14 @@ def main():
     from paper_2508_04484_gb300 import build as B
     from paper_2508_04484_gb300 import dlra as D
     B.build()
-    cfg, mats, w, beams = _workload()
+    cfg, mats, w, beams = _workload(args.workload)
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     K = cfg["n_steps"] if args.energy_steps <= 0 else min(args.energy_steps, cfg["n_steps"])
+    vs_plain = None
+    if len(beams) > 1:
+        vs_plain = _plain_vs_batched(cfg, mats, w, beams, K, args)
     stream = torch.cuda.Stream(device=dev)
-    solver = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
+    solver = D.Solver(dict(cfg, max_concurrent_beams=min(len(beams), 32)), mats, w, beams, stream=stream.cuda_stream)
     nsub = solver.substeps()
     dose = torch.zeros(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -232,7 +271,7 @@ def main():
     for _ in range(args.warmup):
         one_solve()
     torch.cuda.synchronize()
-    log = solver.rank_log()[:K]
+    log = solver.rank_log(0)[:K]
     nsub = nsub[:K]
     r_start, updates, stage_launches = _rank_stats(log, nsub, n)
     clocks = Clocks(dev.index)
@@ -335,7 +374,12 @@ def main():
                 "energy_steps_per_s": value,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": None}
+                "vs_plain": vs_plain}
+        if args.workload != WORKLOAD:
+            line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
+                              "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,
+                              "step": "one whole solve of all beams"}
+            line["beam_energy_steps_per_s"] = value * len(beams)
         print(json.dumps(line))
     solver.close()
     if ws > 1:

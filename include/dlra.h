@@ -72,7 +72,10 @@ enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1 };
  *                           arithmetic, FP64 reductions, factorisations and S).
  *  bk_p, bk_alpha         : Bragg-Kleeman water stopping power S_w(E) = E^(1-p)/(p alpha).
  *  t100                   : water scattering power at 100 MeV, T_w(E) = t100 (100/E)^2.
- *  cuda_stream            : borrowed cudaStream_t for all work; NULL = legacy default.
+ *  max_concurrent_beams   : beams advanced concurrently (one work space and stream pair
+ *                           each; 0 = 8, 1 = one beam after the other).
+ *  cuda_stream            : borrowed cudaStream_t; every call orders its work after what
+ *                           is already enqueued on it. NULL = legacy default stream.
  */
 typedef struct {
   int32_t nx, ny, nz;
@@ -88,6 +91,7 @@ typedef struct {
   double cfl_max;
   int32_t precision;
   double bk_p, bk_alpha, t100;
+  int32_t max_concurrent_beams;
   void* cuda_stream;
 } dlra_config;
 

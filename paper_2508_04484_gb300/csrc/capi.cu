@@ -310,6 +310,18 @@ struct Beam {
   bool active = false;
 };
 
+// Work space of one lane: the buffers of one energy step of one beam and two streams
+// (cell side s0, moment side s1). Beams on different lanes advance concurrently.
+struct Lane {
+  cudaStream_t s0 = nullptr, s1 = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  void *Kb[3] = {nullptr, nullptr, nullptr}, *Xh = nullptr, *Asrc = nullptr;
+  void *Lb[3] = {nullptr, nullptr, nullptr}, *Zm = nullptr, *Wh = nullptr, *L1T = nullptr, *Pst = nullptr;
+  void* GtT = nullptr;
+  double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
+  double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr;
+};
+
 }  // namespace
 
 struct dlra_ctx {
@@ -339,22 +351,17 @@ struct dlra_ctx {
   void* beams = nullptr;   // std::vector<Beam<T>>*
   // shared device buffers (raw pointers, typed at use)
   void *inv_rho = nullptr, *wc = nullptr, *wT = nullptr, *Apm = nullptr;
-  void *Kb[3] = {nullptr, nullptr, nullptr}, *Xh = nullptr, *Asrc = nullptr;
-  void *Lb[3] = {nullptr, nullptr, nullptr}, *Zm = nullptr, *Wh = nullptr, *L1T = nullptr, *Pst = nullptr;
-  void* GtT = nullptr;
   double *rho = nullptr, *f_cell = nullptr, *tau_cell = nullptr;
-  double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
-  double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr, *Gt = nullptr;
   double *coef = nullptr, *sbeta = nullptr;
+  std::vector<Lane> lanes;
+  int max_lanes = 8;
+  cudaEvent_t ev_step = nullptr;
   int* dev_err = nullptr;
   int* schedule_dev = nullptr;
   double* dose_tmp = nullptr;
   // ray sets of the beams (for dlra_reset with retrace)
   std::vector<double*> ray_dev;
   std::vector<int> ray_count;
-  // internal stream for the moment-side (m) work that overlaps the cell-side work
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // streaming-stage kernel timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -449,7 +456,7 @@ void horner_betas(const dlra_ctx* c, double Ea, double hs, double* beta) {
 }
 
 // events around the streaming-stage kernel when profiling is on
-void prof_begin(dlra_ctx* c) {
+void prof_begin(dlra_ctx* c, cudaStream_t st) {
   if (!c->profiling) return;
   if (c->ev_used + 2 > c->ev_pool.size()) {
     for (int i = 0; i < 512; ++i) {
@@ -458,16 +465,17 @@ void prof_begin(dlra_ctx* c) {
       c->ev_pool.push_back(e);
     }
   }
-  cudaEventRecord(c->ev_pool[c->ev_used], c->st);
+  cudaEventRecord(c->ev_pool[c->ev_used], st);
 }
-void prof_end(dlra_ctx* c) {
+void prof_end(dlra_ctx* c, cudaStream_t st) {
   if (!c->profiling) return;
-  cudaEventRecord(c->ev_pool[c->ev_used + 1], c->st);
+  cudaEventRecord(c->ev_pool[c->ev_used + 1], st);
   c->ev_used += 2;
 }
 void prof_collect(dlra_ctx* c) {
   if (c->ev_used == 0) return;
   cudaStreamSynchronize(c->st);
+  for (auto& l : c->lanes) cudaStreamSynchronize(l.s0);
   for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]);
@@ -483,6 +491,7 @@ void prof_collect(dlra_ctx* c) {
 template <typename T>
 struct Engine {
   dlra_ctx* ctx;
+  Lane* L = nullptr;
   std::vector<Beam<T>>& beams() { return *reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams); }
   T* P(void* p) { return reinterpret_cast<T*>(p); }
 
@@ -500,29 +509,29 @@ struct Engine {
   double drop1() const { return sizeof(T) == 8 ? 1e-12 : 3e-4; }
   double drop2() const { return sizeof(T) == 8 ? 1e-8 : 1e-3; }
 
-  // X^ = [X, orth((I - X X^T) K)] with K (n x qcap); X^ in ctx->Xh (n x 2RB)
+  // X^ = [X, orth((I - X X^T) K)] with K (n x qcap); X^ in L->Xh (n x 2RB)
   void augment_x(Beam<T>& B, const T* K, int qcap) {
     const long long n = ctx->n;
     const int RB = ctx->RB;
-    cudaStream_t st = ctx->st;
+    cudaStream_t st = L->s0;
     int64_t& nl = ctx->launches;
-    T* Xh = P(ctx->Xh);
+    T* Xh = P(L->Xh);
     cudaMemsetAsync(Xh + (long long)RB * n, 0, sizeof(T) * n * RB, st);
     cudaMemcpyAsync(Xh, B.X, sizeof(T) * n * RB, cudaMemcpyDeviceToDevice, st);
     const int* rdim = &B.dims->r;
     // C1 = X^T K
-    cudaMemsetAsync(ctx->C1, 0, sizeof(double) * RB * qcap, st);
-    gram<T>(st, n, B.X, n, rdim, RB, qcap, FPlain<T>{K, n, nullptr, qcap}, ctx->C1, RB, nl);
+    cudaMemsetAsync(L->C1, 0, sizeof(double) * RB * qcap, st);
+    gram<T>(st, n, B.X, n, rdim, RB, qcap, FPlain<T>{K, n, nullptr, qcap}, L->C1, RB, nl);
     // R = K - X C1 into X^[:, RB:RB+qcap]
-    apply<T>(st, n, B.X, n, RB, rdim, ctx->C1, RB, qcap, Xh + (long long)RB * n, n, K, T(-1), T(1), nl);
+    apply<T>(st, n, B.X, n, RB, rdim, L->C1, RB, qcap, Xh + (long long)RB * n, n, K, T(-1), T(1), nl);
     for (int pass = 0; pass < 2; ++pass) {
       const int lg = RB + qcap;
-      cudaMemsetAsync(ctx->Cg, 0, sizeof(double) * lg * qcap, st);
-      gram<T>(st, n, Xh, n, nullptr, lg, qcap, FPlain<T>{Xh + (long long)RB * n, n, nullptr, qcap}, ctx->Cg, lg, nl);
-      launch_orth_factor(st, ctx->Cg, pass == 0 ? ctx->C1 : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
-                         ctx->Mapply, &B.dims->qx, ctx->dev_err);
+      cudaMemsetAsync(L->Cg, 0, sizeof(double) * lg * qcap, st);
+      gram<T>(st, n, Xh, n, nullptr, lg, qcap, FPlain<T>{Xh + (long long)RB * n, n, nullptr, qcap}, L->Cg, lg, nl);
+      launch_orth_factor(st, L->Cg, pass == 0 ? L->C1 : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
+                         L->Mapply, &B.dims->qx, ctx->dev_err);
       ++nl;
-      apply<T>(st, n, Xh, n, lg, nullptr, ctx->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl);
+      apply<T>(st, n, Xh, n, lg, nullptr, L->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl);
     }
   }
 
@@ -531,57 +540,57 @@ struct Engine {
     const long long n = ctx->n;
     const int RB = ctx->RB, n2 = ctx->n2, m = ctx->m;
     int64_t& nl = ctx->launches;
-    apply<T>(ctx->st, n, P(ctx->Xh), n, n2, nullptr, ctx->Pt, n2, RB, B.X, n, nullptr, T(1), T(0), nl);
-    gemm<T, 16>(ctx->st, m, RB, n2, ALoadPlain<T>{P(ctx->Wh), m, nullptr, n2},
-                BLoadCol<T, double>{ctx->Qt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.W, m, nullptr, m, T(1), T(0)},
+    apply<T>(L->s0, n, P(L->Xh), n, n2, nullptr, L->Pt, n2, RB, B.X, n, nullptr, T(1), T(0), nl);
+    gemm<T, 16>(L->s0, m, RB, n2, ALoadPlain<T>{P(L->Wh), m, nullptr, n2},
+                BLoadCol<T, double>{L->Qt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.W, m, nullptr, m, T(1), T(0)},
                 nl);
   }
 
   // fork: st2 waits for everything enqueued so far on st
   void fork() {
-    cudaEventRecord(ctx->ev[0], ctx->st);
-    cudaStreamWaitEvent(ctx->st2, ctx->ev[0], 0);
+    cudaEventRecord(L->ev[0], L->s0);
+    cudaStreamWaitEvent(L->s1, L->ev[0], 0);
   }
   // st waits for everything enqueued so far on st2
   void join() {
-    cudaEventRecord(ctx->ev[3], ctx->st2);
-    cudaStreamWaitEvent(ctx->st, ctx->ev[3], 0);
+    cudaEventRecord(L->ev[3], L->s1);
+    cudaStreamWaitEvent(L->s0, L->ev[3], 0);
   }
 
   void streaming(Beam<T>& B, int k) {
     const long long n = ctx->n;
     const int RB = ctx->RB, m = ctx->m, nk = ctx->nk, n2 = ctx->n2;
-    cudaStream_t st = ctx->st;     // cell-side chain
-    cudaStream_t sm = ctx->st2;    // moment-side chain
+    cudaStream_t st = L->s0;     // cell-side chain
+    cudaStream_t sm = L->s1;    // moment-side chain
     int64_t& nl = ctx->launches;
     const int* rdim = &B.dims->r;
-    T* Zm = P(ctx->Zm);
+    T* Zm = P(L->Zm);
     fork();
     // [m] P_k = W^T A^s_d W, packed for the stage kernel; L0 = W S^T
     gemm<T, 16>(sm, (long long)nk * m, RB, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{B.W, m, nullptr, m, rdim, RB}, EpiStoreKBlocks<T>{Zm, m, RB}, nl);
-    cudaMemsetAsync(ctx->P1, 0, sizeof(double) * nk * RB * RB, sm);
-    gram<T>(sm, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, ctx->P1, RB, nl);
-    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, sm>>>(ctx->P1, RB, nk, P(ctx->Pst));
+    cudaMemsetAsync(L->P1, 0, sizeof(double) * nk * RB * RB, sm);
+    gram<T>(sm, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, L->P1, RB, nl);
+    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, sm>>>(L->P1, RB, nk, P(L->Pst));
     ++nl;
-    cudaEventRecord(ctx->ev[1], sm);
-    T* ly = P(ctx->Lb[0]);
-    T* la = P(ctx->Lb[1]);
-    T* lb = P(ctx->Lb[2]);
+    cudaEventRecord(L->ev[1], sm);
+    T* ly = P(L->Lb[0]);
+    T* la = P(L->Lb[1]);
+    T* lb = P(L->Lb[2]);
     gemm<T, 16>(sm, m, RB, RB, ALoadPlain<T>{B.W, m, rdim, RB}, BLoadRow<T, double>{B.S, RB, RB, RB},
                 EpiStore<T>{ly, m, nullptr, m, T(1), T(0)}, nl);
     // [n] G_k = X^T D_k rho^-1 X; K0 = X S (and rho^-1 K0)
-    cudaMemsetAsync(ctx->G1, 0, sizeof(double) * nk * RB * RB, st);
-    gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, ctx->G1, RB, RB, nl);
-    gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(ctx->G1, RB, nk, P(ctx->GtT));
+    cudaMemsetAsync(L->G1, 0, sizeof(double) * nk * RB * RB, st);
+    gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, L->G1, RB, RB, nl);
+    gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(L->G1, RB, nk, P(L->GtT));
     ++nl;
-    cudaEventRecord(ctx->ev[2], st);
-    T* y = P(ctx->Kb[0]);
-    T* va = P(ctx->Kb[1]);
-    T* vb = P(ctx->Kb[2]);
+    cudaEventRecord(L->ev[2], st);
+    T* y = P(L->Kb[0]);
+    T* va = P(L->Kb[1]);
+    T* vb = P(L->Kb[2]);
     apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho));
-    cudaStreamWaitEvent(st, ctx->ev[1], 0);   // stage kernel needs P
-    cudaStreamWaitEvent(sm, ctx->ev[2], 0);   // L-stage needs G
+    cudaStreamWaitEvent(st, L->ev[1], 0);   // stage kernel needs P
+    cudaStreamWaitEvent(sm, L->ev[2], 0);   // L-stage needs G
     // RK4 Horner stages: K-step on st, L-step on sm
     const int ns = ctx->nsub[k];
     const double hs = ctx->h / ns;
@@ -597,11 +606,11 @@ struct Engine {
       const T* lin = ly;
       T* louts[4] = {la, lb, la, ly};
       for (int s2 = 0; s2 < 4; ++s2) {
-        prof_begin(ctx);
-        kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(ctx->Pst), rdim,
+        prof_begin(ctx, st);
+        kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
                   T(beta[s2]), s2 == 3 ? 1 : 0, nl);
-        prof_end(ctx);
-        lstage_kernel<T><<<m, 128, lsmem, sm>>>(P(ctx->Apm), m, nk, lin, ly, louts[s2], P(ctx->GtT), RB, rdim,
+        prof_end(ctx, st);
+        lstage_kernel<T><<<m, 128, lsmem, sm>>>(P(ctx->Apm), m, nk, lin, ly, louts[s2], P(L->GtT), RB, rdim,
                                                  T(beta[s2]));
         ++nl;
         lin = louts[s2];
@@ -609,20 +618,20 @@ struct Engine {
     }
     // augmentation of both bases, then the Galerkin operators on them
     augment_x(B, y, RB);
-    launch_waug<T, T>(sm, B.W, m, RB, ly, m, RB, drop1(), P(ctx->Wh), B.dims);
+    launch_waug<T, T>(sm, B.W, m, RB, ly, m, RB, drop1(), P(L->Wh), B.dims);
     ++nl;
-    T* Xh = P(ctx->Xh);
-    T* Wh = P(ctx->Wh);
-    cudaMemsetAsync(ctx->Gc, 0, sizeof(double) * nk * n2 * n2, st);
-    gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, ctx->Gc, n2, n2, nl);
+    T* Xh = P(L->Xh);
+    T* Wh = P(L->Wh);
+    cudaMemsetAsync(L->Gc, 0, sizeof(double) * nk * n2 * n2, st);
+    gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, L->Gc, n2, n2, nl);
     gemm<T, 16>(sm, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{Wh, m, nullptr, m, nullptr, n2}, EpiStoreKBlocks<T>{Zm, m, n2}, nl);
-    cudaMemsetAsync(ctx->Ph, 0, sizeof(double) * nk * n2 * n2, sm);
-    gram<T>(sm, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, ctx->Ph, n2, nl);
+    cudaMemsetAsync(L->Ph, 0, sizeof(double) * nk * n2 * n2, sm);
+    gram<T>(sm, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, L->Ph, n2, nl);
     join();
-    launch_sstep<T>(st, ctx->Gc, ctx->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, ctx->Sh);
+    launch_sstep<T>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, L->Sh);
     ++nl;
-    launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 0, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
+    launch_svd_truncate<T>(st, L->Sh, n2, RB, rank_params(), k, 0, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
                            ctx->dev_err);
     ++nl;
     apply_truncation(B);
@@ -631,52 +640,59 @@ struct Engine {
   void scattering(Beam<T>& B, int k) {
     const long long n = ctx->n;
     const int RB = ctx->RB, m = ctx->m, M = ctx->M, N = ctx->N;
-    cudaStream_t st = ctx->st;
+    cudaStream_t st = L->s0;
     int64_t& nl = ctx->launches;
     const int* rdim = &B.dims->r;
-    cudaMemsetAsync(ctx->Mg, 0, sizeof(double) * M * RB * RB, st);
-    gram<T>(st, n, B.X, n, rdim, RB, M * RB, FDiag<T>{B.X, n, P(ctx->wc), n, RB, rdim, M}, ctx->Mg, RB, nl);
-    launch_scatter_solve<T>(st, ctx->Mg, M, ctx->coef + (long long)k * M * (N + 1), N, B.S, B.W, m, RB,
-                            P(ctx->L1T), ctx->dev_err);
+    cudaMemsetAsync(L->Mg, 0, sizeof(double) * M * RB * RB, st);
+    gram<T>(st, n, B.X, n, rdim, RB, M * RB, FDiag<T>{B.X, n, P(ctx->wc), n, RB, rdim, M}, L->Mg, RB, nl);
+    launch_scatter_solve<T>(st, L->Mg, M, ctx->coef + (long long)k * M * (N + 1), N, B.S, B.W, m, RB,
+                            P(L->L1T), ctx->dev_err);
     ++nl;
-    launch_qr_lt<T>(st, P(ctx->L1T), m, RB, B.dims, B.W, B.S);
+    launch_qr_lt<T>(st, P(L->L1T), m, RB, B.dims, B.W, B.S);
     ++nl;
   }
 
   void source(Beam<T>& B, int k) {
     const long long n = ctx->n;
     const int RB = ctx->RB, m = ctx->m, M = ctx->M, n2 = ctx->n2;
-    cudaStream_t st = ctx->st;
+    cudaStream_t st = L->s0;
     int64_t& nl = ctx->launches;
-    T* A = P(ctx->Asrc);
+    T* A = P(L->Asrc);
     const double* Bk = B.Bsrc + (long long)k * M * m;
     fork();
-    launch_waug<T, double>(ctx->st2, B.W, m, RB, Bk, m, M, drop1(), P(ctx->Wh), B.dims);
+    launch_waug<T, double>(L->s1, B.W, m, RB, Bk, m, M, drop1(), P(L->Wh), B.dims);
     ++nl;
     src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), B.psi + (long long)k * n, n, M, A);
     ++nl;
     augment_x(B, A, M);
-    cudaMemsetAsync(ctx->XA, 0, sizeof(double) * n2 * M, st);
-    gram<T>(st, n, P(ctx->Xh), n, nullptr, n2, M, FPlain<T>{A, n, nullptr, M}, ctx->XA, n2, nl);
+    cudaMemsetAsync(L->XA, 0, sizeof(double) * n2 * M, st);
+    gram<T>(st, n, P(L->Xh), n, nullptr, n2, M, FPlain<T>{A, n, nullptr, M}, L->XA, n2, nl);
     join();
-    launch_src_assemble<T>(st, B.S, RB, ctx->XA, Bk, P(ctx->Wh), m, M, n2, ctx->h, ctx->Sh);
+    launch_src_assemble<T>(st, B.S, RB, L->XA, Bk, P(L->Wh), m, M, n2, ctx->h, L->Sh);
     ++nl;
-    launch_svd_truncate<T>(st, ctx->Sh, n2, RB, rank_params(), k, 1, ctx->Pt, ctx->Qt, B.S, B.dims, B.rank_log,
+    launch_svd_truncate<T>(st, L->Sh, n2, RB, rank_params(), k, 1, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
                            ctx->dev_err);
     ++nl;
     apply_truncation(B);
   }
 
   void dose(Beam<T>& B) {
-    dose_kernel<T><<<std::min<unsigned>(nblk(ctx->n, 256), 2048), 256, 0, ctx->st>>>(
+    dose_kernel<T><<<std::min<unsigned>(nblk(ctx->n, 256), 2048), 256, 0, L->s0>>>(
         B.X, ctx->n, B.S, B.W, ctx->m, ctx->RB, B.dims, ctx->h * std::sqrt(4.0 * M_PI), B.e_c);
     ++ctx->launches;
   }
 
   dlra_status step_all(int nsteps) {
+    const int nlanes = (int)ctx->lanes.size();
     for (int s = 0; s < nsteps; ++s) {
       const int k = ctx->step;
-      for (auto& B : beams()) {
+      // every lane starts after the work enqueued so far on the context stream
+      cudaEventRecord(ctx->ev_step, ctx->st);
+      for (int l = 0; l < nlanes; ++l) cudaStreamWaitEvent(ctx->lanes[l].s0, ctx->ev_step, 0);
+      auto& bs = beams();
+      for (size_t b = 0; b < bs.size(); ++b) {
+        Beam<T>& B = bs[b];
+        L = &ctx->lanes[b % nlanes];
         if (B.active) {
           streaming(B, k);
           scattering(B, k);
@@ -686,6 +702,11 @@ struct Engine {
           B.active = true;
         }
         if (B.active) dose(B);
+      }
+      // the context stream waits for every lane
+      for (int l = 0; l < nlanes; ++l) {
+        cudaEventRecord(ctx->lanes[l].ev[2], ctx->lanes[l].s0);
+        cudaStreamWaitEvent(ctx->st, ctx->lanes[l].ev[2], 0);
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "kernel launch failed at step %d: %s", k, cudaGetErrorString(e));
@@ -717,33 +738,48 @@ std::vector<Beam<T>>& beams_of(dlra_ctx* ctx) {
 template <typename T>
 dlra_status alloc_shared(dlra_ctx* ctx) {
   const long long n = ctx->n;
-  const int m = ctx->m, RB = ctx->RB, nk = ctx->nk, n2 = ctx->n2;
+  const int m = ctx->m, nk = ctx->nk;
   ALLOC(ctx->inv_rho, sizeof(T) * n);
   ALLOC(ctx->rho, sizeof(double) * n);
   ALLOC(ctx->f_cell, sizeof(double) * n);
   ALLOC(ctx->tau_cell, sizeof(double) * n);
-  for (int i = 0; i < 3; ++i) ALLOC(ctx->Kb[i], sizeof(T) * n * RB);
-  ALLOC(ctx->Xh, sizeof(T) * n * n2);
-  for (int i = 0; i < 3; ++i) ALLOC(ctx->Lb[i], sizeof(T) * m * RB);
-  ALLOC(ctx->Zm, sizeof(T) * (size_t)m * nk * n2);
-  ALLOC(ctx->Wh, sizeof(T) * (size_t)m * n2);
-  ALLOC(ctx->L1T, sizeof(T) * (size_t)m * RB);
-  ALLOC(ctx->Pst, sizeof(T) * (size_t)nk * RB * RB);
-  ALLOC(ctx->GtT, sizeof(T) * (size_t)nk * RB * RB);
   ALLOC(ctx->Apm, sizeof(T) * (size_t)nk * m * m);
-  ALLOC(ctx->G1, sizeof(double) * nk * RB * RB);
-  ALLOC(ctx->P1, sizeof(double) * nk * RB * RB);
-  ALLOC(ctx->Gt, sizeof(double) * nk * RB * RB);
-  ALLOC(ctx->Gc, sizeof(double) * nk * n2 * n2);
-  ALLOC(ctx->Ph, sizeof(double) * nk * n2 * n2);
-  ALLOC(ctx->C1, sizeof(double) * RB * RB);
-  ALLOC(ctx->Cg, sizeof(double) * n2 * RB);
-  ALLOC(ctx->Mapply, sizeof(double) * n2 * RB);
-  ALLOC(ctx->Sh, sizeof(double) * n2 * n2);
-  ALLOC(ctx->Pt, sizeof(double) * n2 * RB);
-  ALLOC(ctx->Qt, sizeof(double) * n2 * RB);
   ALLOC(ctx->dev_err, sizeof(int));
   ALLOC(ctx->dose_tmp, sizeof(double) * n);
+  return DLRA_OK;
+}
+
+// a new lane (work space and streams); needs the number of materials
+template <typename T>
+dlra_status alloc_lane(dlra_ctx* ctx) {
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB, nk = ctx->nk, n2 = ctx->n2, M = ctx->M;
+  ctx->lanes.emplace_back();
+  Lane& L = ctx->lanes.back();
+  CK(cudaStreamCreateWithFlags(&L.s0, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&L.s1, cudaStreamNonBlocking));
+  for (int i = 0; i < 4; ++i) CK(cudaEventCreateWithFlags(&L.ev[i], cudaEventDisableTiming));
+  for (int i = 0; i < 3; ++i) ALLOC(L.Kb[i], sizeof(T) * n * RB);
+  ALLOC(L.Xh, sizeof(T) * n * n2);
+  ALLOC(L.Asrc, sizeof(T) * M * n);
+  for (int i = 0; i < 3; ++i) ALLOC(L.Lb[i], sizeof(T) * m * RB);
+  ALLOC(L.Zm, sizeof(T) * (size_t)m * nk * n2);
+  ALLOC(L.Wh, sizeof(T) * (size_t)m * n2);
+  ALLOC(L.L1T, sizeof(T) * (size_t)m * RB);
+  ALLOC(L.Pst, sizeof(T) * (size_t)nk * RB * RB);
+  ALLOC(L.GtT, sizeof(T) * (size_t)nk * RB * RB);
+  ALLOC(L.G1, sizeof(double) * nk * RB * RB);
+  ALLOC(L.P1, sizeof(double) * nk * RB * RB);
+  ALLOC(L.Gc, sizeof(double) * nk * n2 * n2);
+  ALLOC(L.Ph, sizeof(double) * nk * n2 * n2);
+  ALLOC(L.C1, sizeof(double) * RB * RB);
+  ALLOC(L.Cg, sizeof(double) * n2 * RB);
+  ALLOC(L.Mapply, sizeof(double) * n2 * RB);
+  ALLOC(L.Sh, sizeof(double) * n2 * n2);
+  ALLOC(L.Pt, sizeof(double) * n2 * RB);
+  ALLOC(L.Qt, sizeof(double) * n2 * RB);
+  ALLOC(L.Mg, sizeof(double) * M * RB * RB);
+  ALLOC(L.XA, sizeof(double) * n2 * M);
   return DLRA_OK;
 }
 
@@ -802,9 +838,6 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
   ctx->rho_host = rho;
   ALLOC(ctx->wc, sizeof(T) * M * n);
   ALLOC(ctx->wT, sizeof(T) * M * n);
-  ALLOC(ctx->Asrc, sizeof(T) * M * n);
-  ALLOC(ctx->Mg, sizeof(double) * M * ctx->RB * ctx->RB);
-  ALLOC(ctx->XA, sizeof(double) * ctx->n2 * M);
   CK(cudaMemcpyAsync(ctx->inv_rho, inv_rho.data(), sizeof(T) * n, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->wc, wc.data(), sizeof(T) * wc.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->wT, wT.data(), sizeof(T) * wT.size(), cudaMemcpyHostToDevice, ctx->st));
@@ -937,6 +970,10 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
                                b->weight * pt.second / wsum * ew[e]});
     }
   const int nray = (int)(rays.size() / 8);
+  if ((int)ctx->lanes.size() < ctx->max_lanes && ctx->lanes.size() <= beams_of<T>(ctx).size()) {
+    dlra_status ls = alloc_lane<T>(ctx);
+    if (ls != DLRA_OK) return ls;
+  }
   Beam<T> B;
   ALLOC(B.X, sizeof(T) * n * RB);
   ALLOC(B.W, sizeof(T) * (size_t)m * RB);
@@ -1222,6 +1259,8 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
   if (!(g.bk_p > 1 && g.bk_p < 2 && g.bk_alpha > 0 && g.t100 >= 0))
     return fail(ctx, DLRA_ERR_ARG, "need 1 < bk_p < 2, bk_alpha > 0, t100 >= 0");
   ctx->fp64 = g.precision == DLRA_FP64;
+  if (g.max_concurrent_beams < 0) return fail(ctx, DLRA_ERR_ARG, "max_concurrent_beams must be >= 0");
+  ctx->max_lanes = g.max_concurrent_beams > 0 ? g.max_concurrent_beams : 8;
   if (ctx->fp64 && g.rank_max > 32) return fail(ctx, DLRA_ERR_ARG, "FP64 precision supports rank_max <= 32");
   ctx->st = (cudaStream_t)g.cuda_stream;
   ctx->n = g.nx * g.ny * g.nz;
@@ -1282,8 +1321,7 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
     *out = c.release();
     return s;
   }
-  CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
-  for (int i = 0; i < 4; ++i) CK(cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming));
   if (!ctx->schedule_host.empty()) {
     ALLOC(ctx->schedule_dev, sizeof(int) * ctx->schedule_host.size());
     CK(cudaMemcpy(ctx->schedule_dev, ctx->schedule_host.data(), sizeof(int) * ctx->schedule_host.size(),
@@ -1485,11 +1523,18 @@ const char* dlra_last_error(const dlra_ctx* ctx) { return ctx ? ctx->err.c_str()
 void dlra_destroy(dlra_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
-  if (ctx->st2) cudaStreamSynchronize(ctx->st2);
+  for (auto& l : ctx->lanes) {
+    if (l.s0) cudaStreamSynchronize(l.s0);
+    if (l.s1) cudaStreamSynchronize(l.s1);
+  }
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-  for (cudaEvent_t e : ctx->ev)
-    if (e) cudaEventDestroy(e);
-  if (ctx->st2) cudaStreamDestroy(ctx->st2);
+  for (auto& l : ctx->lanes) {
+    for (cudaEvent_t e : l.ev)
+      if (e) cudaEventDestroy(e);
+    if (l.s0) cudaStreamDestroy(l.s0);
+    if (l.s1) cudaStreamDestroy(l.s1);
+  }
+  if (ctx->ev_step) cudaEventDestroy(ctx->ev_step);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->beams) {
     if (ctx->fp64) free_beams<double>(ctx);

@@ -39,7 +39,7 @@ class dlra_config(C.Structure):
                 ("e_max", C.c_double), ("e_min", C.c_double), ("n_energy_steps", C.c_int32),
                 ("cfl_max", C.c_double), ("precision", C.c_int32),
                 ("bk_p", C.c_double), ("bk_alpha", C.c_double), ("t100", C.c_double),
-                ("cuda_stream", C.c_void_p)]
+                ("max_concurrent_beams", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class dlra_material(C.Structure):
@@ -142,6 +142,7 @@ def make_config(cfg: dict, stream=None):
     c.bk_p = float(cfg.get("bk_p", 1.77))
     c.bk_alpha = float(cfg.get("bk_alpha", 0.0022))
     c.t100 = float(cfg.get("t100", 1.72e-4))
+    c.max_concurrent_beams = int(cfg.get("max_concurrent_beams", 0))
     c.cuda_stream = stream
     sched = cfg.get("rank_schedule")
     keep = None

@@ -150,3 +150,14 @@ def phantom_64cube_8beams(seed=5):
     for b in beams:
         b["weight"] = float(rng.uniform(0.5, 1.5))
     return cfg, mats, w, beams
+
+
+def phantom_48cube_8beams(seed=6):
+    """48^3 voxels of 2 mm, phantom seed 6, 8 beams (60-100 MeV, 30 degree cone), N=11,
+    adaptive rank (tol 1e-3, <= 24), 120 energy steps: the batched-beam comparison case."""
+    cfg = base_config(nx=48, ny=48, nz=48, dx=0.2, dy=0.2, dz=0.2, N=11, collision=BOLTZMANN,
+                      transport_correction=1, rank_mode=ADAPTIVE, rank=24, rank_max=24, trunc_tol=1e-3,
+                      e_max=100.0, e_min=1.0, n_steps=120, precision=FP32_MIXED)
+    mats, w = ellipsoid_phantom(cfg, seed, n_incl=8, semi=(0.4, 1.8))
+    beams = cone_beams(cfg, 8, seed, e_range=(60.0, 100.0))
+    return cfg, mats, w, beams
