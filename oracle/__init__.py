@@ -17,6 +17,8 @@ Modules (each function cites the part of the paper it follows):
 * ``raytrace`` -- CSDA uncollided ray tracer (Sec. 3.2, without straggling).
 * ``fullrank`` -- full-rank solve with the same split and integrators (Sec. 4).
 * ``dlra``     -- the augmented-BUG low-rank energy step (Sec. 2.2, Sec. 3.3.3).
+* ``adjoint``  -- discrete adjoint of the full-rank solve: gradients of a loss of the
+                  deposited energy with respect to beam and mixture weights.
 
 Parity status of each function is stated in its module header; where a
 function has no independent pin it says "parity unpinned".

@@ -13,7 +13,9 @@ every face, i.e. vacuum inflow; the collided flux has no external source.
 Pins (tests/test_oracle_grid.py): the explicit sparse matrices assembled entry by
 entry from the paper's coefficients; second-order convergence on a smooth
 function; telescoping of the cell sum of the upwind operator to the boundary
-flux (3 u_n - u_{n-1})/2.
+flux (3 u_n - u_{n-1})/2. The transposed application ``apply_DT`` (used by the
+discrete adjoint) is pinned against the transpose of the assembled matrix
+(tests/test_oracle_adjoint.py).
 """
 from __future__ import annotations
 
@@ -42,6 +44,30 @@ def apply_D(Y: np.ndarray, dims, d: int, sign: int, delta: float) -> np.ndarray:
         out = (3.0 * V - 4.0 * shifted(+1) + shifted(+2)) / (2.0 * delta)
     else:
         out = (-3.0 * V + 4.0 * shifted(-1) - shifted(-2)) / (2.0 * delta)
+    return out.reshape(-1, c)
+
+
+def apply_DT(Y: np.ndarray, dims, d: int, sign: int, delta: float) -> np.ndarray:
+    """((D^{sign}_d)^T Y): row i of D^{sign}_d holds coef_o / (2 delta) at column i + sign*o
+    (o = 0, 1, 2; coef = sign * (3, -4, 1)), so column j of D^T Y gathers coef_o Y[j - sign*o]
+    over the rows j - sign*o inside the grid (zero ghost layers, as in apply_D)."""
+    nx, ny, nz = dims
+    c = Y.shape[1]
+    V = Y.reshape(nz, ny, nx, c)
+    ax = AXIS_OF[d]
+    pad = [(0, 0)] * 4
+    pad[ax] = (2, 2)
+    P = np.pad(V, pad)
+    L = V.shape[ax]
+
+    def shifted(s):
+        sl = [slice(None)] * 4
+        sl[ax] = slice(2 + s, 2 + s + L)
+        return P[tuple(sl)]
+
+    out = np.zeros_like(V)
+    for o, coef in ((0, 3.0), (1, -4.0), (2, 1.0)):
+        out = out + sign * coef / (2.0 * delta) * shifted(-sign * o)
     return out.reshape(-1, c)
 
 

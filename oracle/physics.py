@@ -33,26 +33,32 @@ FOKKER_PLANCK = 0
 BOLTZMANN = 1
 
 
+def _num(x):
+    """x as a float64 array, or complex128 when x is complex (complex-step derivatives)."""
+    x = np.asarray(x)
+    return x.astype(np.result_type(x, np.float64))
+
+
 def stopping_power_water(E, p, alpha):
     """S_w(E) = E^(1-p) / (p alpha)  [MeV/cm]."""
-    E = np.asarray(E, dtype=np.float64)
+    E = _num(E)
     return E ** (1.0 - p) / (p * alpha)
 
 
 def range_water(E, p, alpha):
     """CSDA range R_w(E) = int_0^E dE'/S_w(E') = alpha E^p  [cm]."""
-    E = np.asarray(E, dtype=np.float64)
+    E = _num(E)
     return alpha * E ** p
 
 
 def energy_from_range_water(R, p, alpha):
-    R = np.asarray(R, dtype=np.float64)
-    return (np.maximum(R, 0.0) / alpha) ** (1.0 / p)
+    R = _num(R)
+    return (np.where(np.real(R) > 0.0, R, 0.0) / alpha) ** (1.0 / p)
 
 
 def scattering_power_water(E, t100):
     """T_w(E) = t100 (100/E)^2  [rad^2/cm]."""
-    E = np.asarray(E, dtype=np.float64)
+    E = _num(E)
     return t100 * (100.0 / E) ** 2
 
 
@@ -170,7 +176,7 @@ class PhysicsTables:
         Boltzmann: Sigma_t = G_0 = sigma_0 (minus sigma_{N+1} under the correction);
         Fokker-Planck: 0.
         """
-        E = np.asarray(E, dtype=np.float64)
+        E = _num(E)
         if self.collision != BOLTZMANN:
             return np.zeros_like(E)
         s, xi = self._unit[i]

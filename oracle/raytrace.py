@@ -25,6 +25,10 @@ deposit integrals are evaluated by nested Gauss-Legendre quadrature of their
 definitions, written in the energy variable (ds = dE / S(x, E)), which stays
 smooth up to the end of the range.
 
+Every branch decides on real parts only, so the tracer also runs on complex mixture
+weights: the complex-step derivative Im f(w + i h e) / h (Squire and Trapp, 1998) is then
+the exact derivative of this tracer, which ``trace_vjp`` uses for the discrete adjoint.
+
 Pins (tests/test_oracle_raytrace.py): homogeneous water, normal incidence: the
 closed form N(s) = exp(-int Sigma_t ds) with E(s) = ((R_0 - s)/alpha)^(1/p); the
 energy balance E_in N_in = deposit + removed + exit + cut-off energy; the
@@ -125,9 +129,9 @@ def _segments(o, v, prob):
 
 
 class RayTraceResult:
-    def __init__(self, K, n):
-        self.psi = np.zeros((K, n))     # bin-averaged uncollided fluence  [1/(cm^2 MeV)]
-        self.e_u = np.zeros(n)          # uncollided energy deposit        [MeV/cm^3]
+    def __init__(self, K, n, dtype=np.float64):
+        self.psi = np.zeros((K, n), dtype=dtype)    # bin-averaged uncollided fluence  [1/(cm^2 MeV)]
+        self.e_u = np.zeros(n, dtype=dtype)         # uncollided energy deposit        [MeV/cm^3]
         self.removed_energy = 0.0       # energy carried into the collided flux
         self.removed_particles = 0.0
         self.exit_energy = 0.0          # energy of uncollided protons leaving the box
@@ -138,9 +142,9 @@ class RayTraceResult:
 def trace(prob, beam, nq: int = 12) -> RayTraceResult:
     """Trace one beam through the phantom of ``prob`` (see module docstring)."""
     p, alpha = prob.phys.p, prob.phys.alpha
-    res = RayTraceResult(prob.K, prob.n)
+    res = RayTraceResult(prob.K, prob.n, np.result_type(prob.w, np.float64))
     # material factors per cell
-    f_cell = np.zeros(prob.n)
+    f_cell = np.zeros(prob.n, dtype=np.result_type(prob.w, np.float64))
     for i, m in enumerate(prob.phys.mats):
         f_cell += prob.w[i] * m.density * m.sp_ratio
     Emin = prob.e_min
@@ -177,39 +181,39 @@ def trace(prob, beam, nq: int = 12) -> RayTraceResult:
             f = f_cell[cell]
             ell = tb - ta
             Rb = R - f * ell
-            stop = Rb <= Rmin
+            stop = Rb.real <= Rmin
             if stop:
                 ell = (R - Rmin) / f
                 Rb = Rmin
             # split the segment at bin boundaries (ranges R_k of the grid energies)
             cuts = [0.0]
-            inside = Rbin[(Rbin < R) & (Rbin > Rb)]
+            inside = Rbin[(Rbin < np.real(R)) & (Rbin > Rb.real)]
             for Rk in sorted(inside, reverse=True):
                 cuts.append((R - Rk) / f)
             cuts.append(ell)
             for sa, sb in zip(cuts[:-1], cuts[1:]):
-                if sb - sa <= 0.0:
+                if np.real(sb - sa) <= 0.0:
                     continue
-                Ehi = float(physics.energy_from_range_water(R - f * sa, p, alpha))
-                Elo = float(physics.energy_from_range_water(R - f * sb, p, alpha))
-                kbin = int(np.searchsorted(-prob.E, -0.5 * (Ehi + Elo)) - 1)
+                Ehi = physics.energy_from_range_water(R - f * sa, p, alpha)
+                Elo = physics.energy_from_range_water(R - f * sb, p, alpha)
+                kbin = int(np.searchsorted(-prob.E, -0.5 * np.real(Ehi + Elo)) - 1)
                 kbin = min(max(kbin, 0), prob.K - 1)
                 # integrals over the sub-segment written in the energy variable, ds = dE / S(x, E)
                 E = 0.5 * (Ehi - Elo) * xg + 0.5 * (Ehi + Elo)
                 wE = 0.5 * (Ehi - Elo) * wg
                 Sx = stopping_cell(cell, E)
-                NE = np.empty(nq)
+                NE = np.empty(nq, dtype=res.psi.dtype)
                 for j in range(nq):
                     # N(E) = N(Ehi) exp(-int_E^Ehi Sigma_t / S dE')
                     Ei = 0.5 * (Ehi - E[j]) * xg + 0.5 * (Ehi + E[j])
                     wi = 0.5 * (Ehi - E[j]) * wg
-                    NE[j] = N * math.exp(-np.sum(wi * sigma_t_vec(cell, Ei) / stopping_cell(cell, Ei)))
+                    NE[j] = N * np.exp(-np.sum(wi * sigma_t_vec(cell, Ei) / stopping_cell(cell, Ei)))
                 st = sigma_t_vec(cell, E)
                 res.psi[kbin, cell] += wr * np.sum(wE * NE / Sx) / (V * prob.h)
                 res.e_u[cell] += wr * np.sum(wE * NE) / V
                 res.removed_energy += wr * np.sum(wE * st * NE * E / Sx)
                 res.removed_particles += wr * np.sum(wE * st * NE / Sx)
-                N = N * math.exp(-np.sum(wE * st / Sx))
+                N = N * np.exp(-np.sum(wE * st / Sx))
             R = Rb
             if stop:
                 res.cutoff_energy += wr * N * Emin
@@ -218,3 +222,34 @@ def trace(prob, beam, nq: int = 12) -> RayTraceResult:
         if alive:
             res.exit_energy += wr * N * physics.energy_from_range_water(R, p, alpha)
     return res
+
+
+def crossed_cells(prob, beam):
+    """Cells that at least one ray of the beam crosses (the only cells ``trace`` reads)."""
+    cells = set()
+    for (o, v, _, _) in beam_rays(beam, prob):
+        for cell, _, _ in _segments(o, v, prob):
+            cells.add(cell)
+    return sorted(cells)
+
+
+def trace_vjp(prob, beam, gpsi, geu, nq: int = 12, h: float = 1e-30):
+    """Vector-Jacobian product of ``trace`` with respect to the mixture weights.
+
+    Returns dw (M, n) with dw[i, x] = sum_{k, y} gpsi[k, y] d psi[k, y] / d w_i(x)
+    + sum_y geu[y] d e_u[y] / d w_i(x), each derivative taken by the complex step
+    Im trace(w + i h e_{i,x}) / h, which has no cancellation, for every cell a ray
+    crosses (the tracer reads no other cell, so the derivative is zero there).
+    """
+    import copy
+
+    dw = np.zeros((prob.M, prob.n))
+    pc = copy.copy(prob)
+    for i in range(prob.M):
+        for x in crossed_cells(prob, beam):
+            wc = prob.w.astype(np.complex128)
+            wc[i, x] += 1j * h
+            pc.w = wc
+            r = trace(pc, beam, nq)
+            dw[i, x] = (np.sum(gpsi * r.psi.imag) + np.sum(geu * r.e_u.imag)) / h
+    return dw
