@@ -9,8 +9,9 @@
  * self-scattering by an implicit-Euler L-step, and the first-collision source of
  * a CSDA ray tracer (Sec. 3.2) by augmented BUG K/L/S steps with explicit Euler.
  *
- * Units: cm, MeV, g/cm^3. Doses are per unit beam weight (one source proton for
- * weight 1); 2-D slabs (ny == 1, dy == 0) are per unit length in y.
+ * Units: cm, MeV, g/cm^3. Each beam is solved at unit weight (one source proton)
+ * and enters the dose times its weight; 2-D slabs (ny == 1, dy == 0) are per unit
+ * length in y.
  *
  * Conventions for every entry point:
  *  - All functions return a dlra_status; no exception crosses the ABI.
@@ -118,7 +119,9 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out);
 /* Set the mixture (Sec. 2.1): n_mat base materials and weights w [n_mat][n] (cell
  * order of Sec. 3.3.2), w_m(x) >= 0 summing to 1 per cell. w may be host or device
  * memory (w_on_device); it is copied. Computes the per-step physics tables and the
- * streaming sub-step counts. Must precede dlra_add_beam. */
+ * streaming sub-step counts. Must precede dlra_add_beam. May be called again with the
+ * same n_mat (new materials and weights): every beam is then retraced and rewound to
+ * E_max as by dlra_reset(ctx, 1). */
 dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material* mats,
                                const double* w, int32_t w_on_device);
 
@@ -133,7 +136,7 @@ dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id
  * Fails with DLRA_ERR_STATE past the last energy step. */
 dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps);
 
-/* Dose e(x) = collided + uncollided deposited energy [MeV/cm^3] summed over beams,
+/* Dose e(x) = weighted sum over beams of collided + uncollided deposited energy [MeV/cm^3]
  * (per_mass = 1: divided by the density of the mixture, MeV/g). out [n] doubles,
  * host or device memory. The collided part accumulates dE sqrt(4 pi) u_0(x) after
  * every energy step. Synchronises the stream when out is a host pointer. */
@@ -174,6 +177,33 @@ dlra_status dlra_get_substeps(dlra_ctx* ctx, int32_t* nsub);
  * low-rank state, dose and rank log; retrace = 1 reruns the ray tracer of every
  * beam into its existing buffers. Enqueued on the context's stream; allocates nothing. */
 dlra_status dlra_reset(dlra_ctx* ctx, int32_t retrace);
+
+/* Set the weight of one beam (>= 0): the dose is sum_b weight_b e_b with e_b the
+ * beam's deposit at unit weight, so a new weight takes effect at the next dlra_dose
+ * without stepping again. */
+dlra_status dlra_set_beam_weight(dlra_ctx* ctx, int32_t beam_id, double weight);
+
+/* Prepare the reverse sweep (dlra_backward): from the next dlra_step on, every
+ * beam's low-rank state is copied on the device at the start of energy steps 0,
+ * I, 2I, ... (I = checkpoint_interval >= 1; 0 switches it off). Must be called at
+ * step 0 (after dlra_init or dlra_reset). Memory: ceil(K/I) states per beam. */
+dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval);
+
+/* Gradient of a loss L(e) of the dose e(x) (MeV/cm^3, the quantity of dlra_dose with
+ * per_mass = 0) after the energy steps run so far, by the discrete adjoint of those
+ * steps (the paper states only the forward method). Input dL_de [n] (host or device,
+ * in_on_device). Outputs, either may be NULL:
+ *   dL_dweight [n_beams] (host): dL/d weight_b = <dL/de, e_b> (exact; e_b at unit weight);
+ *   dL_dw [n_mat][n] (host or device, out_on_device): dL/dw_m(x) through the stopping
+ *     power S(x, E) = sum_m w_m S_m(E) in streaming and collisions, the scattering and
+ *     first-collision coefficients (Sec. 2.1, Eq. mixXS) and the ray tracer (Sec. 3.2).
+ * The adjoint state is a low-rank factorisation advanced by the same BUG steps with
+ * the transposed operators (its rank control: the forward's, adaptive when the forward
+ * replays a schedule); forward states are recomputed from the checkpoints of
+ * dlra_enable_adjoint, one segment at a time. Requires dlra_enable_adjoint before the
+ * first step (else DLRA_ERR_STATE). Synchronises. The forward state is unchanged. */
+dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
+                          double* dL_dw, int32_t out_on_device);
 
 /* Per-kernel timing with CUDA events on the context's stream. enable = 1 records an
  * event pair around every launch of the fused streaming-stage kernel (the K-step

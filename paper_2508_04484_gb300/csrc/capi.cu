@@ -41,25 +41,28 @@ namespace {
 // small helper kernels
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void pstack_kernel(const double* __restrict__ P, int RB, int nk, T* __restrict__ Pst) {
-  // Pst[(c' * nk + k) * RB + c] = P_k[c'][c], P_k[a][b] at P[(k*RB + b)*RB + a]
+__global__ void pstack_kernel(const double* __restrict__ P, int RB, int nk, T* __restrict__ Pst, int adj) {
+  // Pst[(c' * nk + k) * RB + c] = P_k[c'][c], P_k[a][b] at P[(k*RB + b)*RB + a].
+  // adj: the transposed streaming operator pairs D^-_d with -P^-_d and D^+_d with -P^+_d
+  // ((D^-)^T = -D^+ for the zero-ghost stencils), i.e. block k takes -P_{k xor 1}.
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   int tot = nk * RB * RB;
   if (e >= tot) return;
   int c = e % RB, row = e / RB;
   int k = row % nk, cp = row / nk;
-  Pst[e] = T(P[((long long)k * RB + c) * RB + cp]);
+  const double v = P[((long long)(adj ? (k ^ 1) : k) * RB + c) * RB + cp];
+  Pst[e] = T(adj ? -v : v);
 }
 
 template <typename T>
-__global__ void gt_kernel(const double* __restrict__ G, int RB, int nk, T* __restrict__ GT) {
-  // GT[(k*RB + c)*RB + a] = G_k[c][a] = G[(k*RB + a)*RB + c]
+__global__ void gt_kernel(const double* __restrict__ G, int RB, int nk, T* __restrict__ GT, int adj) {
+  // GT[(k*RB + c)*RB + a] = G_k[c][a] = G[(k*RB + a)*RB + c]; adj (transposed operator): GT_k = G_k
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   int tot = nk * RB * RB;
   if (e >= tot) return;
   int a = e % RB, j = e / RB;
   int k = j / RB, c = j % RB;
-  GT[e] = T(G[((long long)k * RB + a) * RB + c]);
+  GT[e] = T(adj ? G[e] : G[((long long)k * RB + a) * RB + c]);
 }
 
 template <typename T>
@@ -113,9 +116,14 @@ __global__ void to_double_kernel(const T* __restrict__ in, double* __restrict__ 
 }
 
 __global__ void dose_total_kernel(const double* __restrict__ ec, const double* __restrict__ eu, long long n,
-                                  int first, double* __restrict__ out) {
+                                  int first, double weight, double* __restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (first ? 0.0 : out[i]) + ec[i] + eu[i];
+  if (i < n) out[i] = (first ? 0.0 : out[i]) + weight * (ec[i] + eu[i]);
+}
+
+__global__ void scale_kernel(const double* __restrict__ in, double a, long long n, double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * in[i];
 }
 
 __global__ void div_kernel(double* __restrict__ out, const double* __restrict__ rho, long long n) {
@@ -295,6 +303,15 @@ struct Base {
   virtual ~Base() {}
 };
 
+// a copy of one low-rank state (checkpoints and replayed states of the reverse sweep)
+template <typename T>
+struct Snap {
+  T* X = nullptr;
+  T* W = nullptr;
+  double* S = nullptr;
+  BeamDims* dims = nullptr;
+};
+
 template <typename T>
 struct Beam {
   T* X = nullptr;
@@ -302,12 +319,36 @@ struct Beam {
   double* S = nullptr;
   BeamDims* dims = nullptr;
   int* rank_log = nullptr;
-  double* psi = nullptr;
-  double* e_u = nullptr;
-  double* e_c = nullptr;
+  double* psi = nullptr;      // fluence of every energy bin at unit beam weight
+  double* e_u = nullptr;      // uncollided deposit at unit weight
+  double* e_c = nullptr;      // collided deposit at unit weight
   double* Bsrc = nullptr;
   std::vector<int> has_src;
+  int first_src = -1;         // first energy step with a first-collision source
+  double weight = 1.0;        // beam weight: the beam's deposit enters the dose times weight
+  double dir[3] = {0, 0, 1};
   bool active = false;
+  std::vector<Snap<T>> ckpt;  // states at the start of steps 0, I, 2I, ... (adjoint enabled)
+};
+
+// Work space of the reverse sweep (allocated on the first dlra_backward).
+template <typename T>
+struct AdjWork {
+  Beam<T> mu;                 // adjoint state, its own low-rank factors and rank log
+  Snap<T> alpha;              // adjoint state after the adjoint collision step
+  Beam<T> rep;                // forward state replayed from a checkpoint
+  std::vector<Snap<T>> seg;   // forward states at the start of each step of a segment
+  T* capf = nullptr;          // forward K-stage inputs rho^-1 z of one energy step
+  T* capa = nullptr;          // their adjoints
+  int cap_ns = 0;
+  T* gvec = nullptr;          // dL/de in the n-side type
+  double *ge = nullptr, *be0 = nullptr, *gtmp = nullptr;
+  double *grad_rho = nullptr, *grad_f = nullptr, *grad_tau = nullptr, *grad_w = nullptr, *dw = nullptr;
+  double *Cm = nullptr, *Cl = nullptr, *ysrc = nullptr, *mcoef = nullptr, *dbeta = nullptr;
+  std::vector<double*> gpsi;  // dL/dpsi per beam (K x n)
+  int nb_cap = 0;
+  void* ray_scratch = nullptr;
+  size_t ray_scratch_bytes = 0;
 };
 
 // Work space of one lane: the buffers of one energy step of one beam and two streams
@@ -357,11 +398,17 @@ struct dlra_ctx {
   int max_lanes = 8;
   cudaEvent_t ev_step = nullptr;
   int* dev_err = nullptr;
+  int* flags_dev = nullptr;
   int* schedule_dev = nullptr;
   double* dose_tmp = nullptr;
   // ray sets of the beams (for dlra_reset with retrace)
   std::vector<double*> ray_dev;
   std::vector<int> ray_count;
+  // reverse sweep: checkpoint interval (0 = off) and its work space (AdjWork<T>*)
+  int ckpt_interval = 0;
+  void* adj = nullptr;
+  std::vector<double> tau_coef;   // per material: Sigma_t / T_w factor rho_i kappa_i g0_i
+  size_t sbeta_cap = 0;
   // streaming-stage kernel timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -490,20 +537,40 @@ void prof_collect(dlra_ctx* c) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Engine {
+  void snap_save(const Beam<T>& B, Snap<T>& s, cudaStream_t st) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, m = ctx->m;
+    cudaMemcpyAsync(s.X, B.X, sizeof(T) * n * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s.W, B.W, sizeof(T) * (size_t)m * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s.S, B.S, sizeof(double) * RB * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s.dims, B.dims, sizeof(BeamDims), cudaMemcpyDeviceToDevice, st);
+  }
+  void snap_load(const Snap<T>& s, Beam<T>& B, cudaStream_t st) {
+    const long long n = ctx->n;
+    const int RB = ctx->RB, m = ctx->m;
+    cudaMemcpyAsync(B.X, s.X, sizeof(T) * n * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(B.W, s.W, sizeof(T) * (size_t)m * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(B.S, s.S, sizeof(double) * RB * RB, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(B.dims, s.dims, sizeof(BeamDims), cudaMemcpyDeviceToDevice, st);
+  }
+
   dlra_ctx* ctx;
   Lane* L = nullptr;
   std::vector<Beam<T>>& beams() { return *reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams); }
   T* P(void* p) { return reinterpret_cast<T*>(p); }
 
+  bool adj_rank = false;   // the reverse sweep's own rank control (no schedule replay)
+
   RankParams rank_params() {
     RankParams rp;
     rp.mode = ctx->cfg.rank_mode;
+    if (adj_rank && rp.mode == DLRA_RANK_SCHEDULE) rp.mode = DLRA_RANK_ADAPTIVE;
     rp.rank = ctx->cfg.rank;
     rp.rank_max = ctx->RB;
     rp.tol = ctx->cfg.trunc_tol;
     rp.nz_tol = sizeof(T) == 8 ? 1e-14 : 1e-6;
     rp.cluster_tol = sizeof(T) == 8 ? 1e-10 : 1e-5;
-    rp.schedule = ctx->schedule_dev;
+    rp.schedule = adj_rank ? nullptr : ctx->schedule_dev;
     return rp;
   }
   double drop1() const { return sizeof(T) == 8 ? 1e-12 : 3e-4; }
@@ -557,7 +624,13 @@ struct Engine {
     cudaStreamWaitEvent(L->s0, L->ev[3], 0);
   }
 
-  void streaming(Beam<T>& B, int k) {
+  // Streaming BUG step of Eq. KLS over one energy step (K-, L-, S-steps with n_sub RK4
+  // sub-steps each, augmentation, truncation). adj = 1 integrates the transposed operator
+  // (reverse sweep): the K-stage kernel applies sum_d rho^-1 [(D^-_d)^T K P^+_d + (D^+_d)^T K P^-_d],
+  // the L-step uses G_k instead of G_k^T and the S-step G_k^T instead of G_k.
+  // cap (n x RB buffers, stride n RB): forward, the stage inputs rho^-1 z of every sub-step
+  // j and stage s at cap[4j + s]; adjoint (required), the adjoint of that stage input.
+  void streaming(Beam<T>& B, int k, int adj = 0, T* cap = nullptr) {
     const long long n = ctx->n;
     const int RB = ctx->RB, m = ctx->m, nk = ctx->nk, n2 = ctx->n2;
     cudaStream_t st = L->s0;     // cell-side chain
@@ -565,13 +638,15 @@ struct Engine {
     int64_t& nl = ctx->launches;
     const int* rdim = &B.dims->r;
     T* Zm = P(L->Zm);
+    const long long nrb = n * RB;
+    auto capq = [&](int q) { return cap + (long long)q * nrb; };
     fork();
     // [m] P_k = W^T A^s_d W, packed for the stage kernel; L0 = W S^T
     gemm<T, 16>(sm, (long long)nk * m, RB, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{B.W, m, nullptr, m, rdim, RB}, EpiStoreKBlocks<T>{Zm, m, RB}, nl);
     cudaMemsetAsync(L->P1, 0, sizeof(double) * nk * RB * RB, sm);
     gram<T>(sm, m, B.W, m, rdim, RB, nk * RB, FPlain<T>{Zm, m, nullptr, nk * RB}, L->P1, RB, nl);
-    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, sm>>>(L->P1, RB, nk, P(L->Pst));
+    pstack_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, sm>>>(L->P1, RB, nk, P(L->Pst), adj);
     ++nl;
     cudaEventRecord(L->ev[1], sm);
     T* ly = P(L->Lb[0]);
@@ -582,13 +657,14 @@ struct Engine {
     // [n] G_k = X^T D_k rho^-1 X; K0 = X S (and rho^-1 K0)
     cudaMemsetAsync(L->G1, 0, sizeof(double) * nk * RB * RB, st);
     gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, L->G1, RB, RB, nl);
-    gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(L->G1, RB, nk, P(L->GtT));
+    gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(L->G1, RB, nk, P(L->GtT), adj);
     ++nl;
     cudaEventRecord(L->ev[2], st);
     T* y = P(L->Kb[0]);
-    T* va = P(L->Kb[1]);
+    T* va = (cap && !adj) ? capq(0) : P(L->Kb[1]);
     T* vb = P(L->Kb[2]);
-    apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho));
+    if (adj) apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl);
+    else apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho));
     cudaStreamWaitEvent(st, L->ev[1], 0);   // stage kernel needs P
     cudaStreamWaitEvent(sm, L->ev[2], 0);   // L-stage needs G
     // RK4 Horner stages: K-step on st, L-step on sm
@@ -598,20 +674,40 @@ struct Engine {
         ((size_t)nk * m + (size_t)nk * RB * RB + (size_t)(128 / (RB <= 32 ? 32 : 64)) * nk * RB) * sizeof(T);
     if (lsmem > 48 * 1024)
       cudaFuncSetAttribute(lstage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
-    for (int j = 0; j < ns; ++j) {
+    for (int jj = 0; jj < ns; ++jj) {
+      // the transposed K-step runs the sub-steps backwards (their adjoints pair with the
+      // forward stages of the same sub-step); the polynomials of one energy step commute,
+      // so the L-step keeps the forward order
+      const int j = adj ? ns - 1 - jj : jj;
       double beta[4];
       horner_betas(ctx, ctx->E[k] - j * hs, hs, beta);
+      if (adj) cudaMemcpyAsync(va, y, sizeof(T) * nrb, cudaMemcpyDeviceToDevice, st);
       const T* vins[4] = {va, vb, va, vb};
       T* vouts[4] = {vb, va, vb, va};
       const T* lin = ly;
       T* louts[4] = {la, lb, la, ly};
       for (int s2 = 0; s2 < 4; ++s2) {
         prof_begin(ctx, st);
-        kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                  T(beta[s2]), s2 == 3 ? 1 : 0, nl);
+        if (adj) {
+          // adjoint stage s2 uses the outermost remaining Horner factor and produces the
+          // adjoint of the input of forward stage 3 - s2
+          const int sf = 3 - s2;
+          const T* vin = s2 == 0 ? va : capq(4 * j + sf + 1);
+          kstage<T>(RB, st, vin, y, y, capq(4 * j + sf), n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
+                    T(beta[sf]), 2, nl);
+        } else if (cap) {
+          T* vout = s2 < 3 ? capq(4 * j + s2 + 1) : (j + 1 < ns ? capq(4 * (j + 1)) : vb);
+          kstage<T>(RB, st, capq(4 * j + s2), y, y, vout, n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl);
+        } else {
+          kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl);
+        }
         prof_end(ctx, st);
+        double lbeta[4];
+        horner_betas(ctx, ctx->E[k] - jj * hs, hs, lbeta);
         lstage_kernel<T><<<m, 128, lsmem, sm>>>(P(ctx->Apm), m, nk, lin, ly, louts[s2], P(L->GtT), RB, rdim,
-                                                 T(beta[s2]));
+                                                 T(lbeta[s2]));
         ++nl;
         lin = louts[s2];
       }
@@ -624,6 +720,10 @@ struct Engine {
     T* Wh = P(L->Wh);
     cudaMemsetAsync(L->Gc, 0, sizeof(double) * nk * n2 * n2, st);
     gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, L->Gc, n2, n2, nl);
+    if (adj) {
+      launch_transpose_blocks(st, L->Gc, n2, nk);
+      ++nl;
+    }
     gemm<T, 16>(sm, (long long)nk * m, n2, m, ALoadRowMajor<T>{P(ctx->Apm), m, m},
                 BLoadCol<T, T>{Wh, m, nullptr, m, nullptr, n2}, EpiStoreKBlocks<T>{Zm, m, n2}, nl);
     cudaMemsetAsync(L->Ph, 0, sizeof(double) * nk * n2 * n2, sm);
@@ -653,22 +753,30 @@ struct Engine {
   }
 
   void source(Beam<T>& B, int k) {
+    source_with(B, k, nullptr, B.Bsrc + (long long)k * ctx->M * ctx->m, ctx->M, B.psi + (long long)k * ctx->n);
+  }
+
+  // Explicit-Euler source BUG step (Sec. 3.3.3 steps 2-4) for a rank-Ms source h A Bk^T:
+  // A (n x Ms) given, or (A == nullptr) w_i(x) psi(x) built from the fluence psi.
+  void source_with(Beam<T>& B, int k, const T* Ain, const double* Bk, int Ms, const double* psi) {
     const long long n = ctx->n;
-    const int RB = ctx->RB, m = ctx->m, M = ctx->M, n2 = ctx->n2;
+    const int RB = ctx->RB, m = ctx->m, n2 = ctx->n2;
     cudaStream_t st = L->s0;
     int64_t& nl = ctx->launches;
-    T* A = P(L->Asrc);
-    const double* Bk = B.Bsrc + (long long)k * M * m;
     fork();
-    launch_waug<T, double>(L->s1, B.W, m, RB, Bk, m, M, drop1(), P(L->Wh), B.dims);
+    launch_waug<T, double>(L->s1, B.W, m, RB, Bk, m, Ms, drop1(), P(L->Wh), B.dims);
     ++nl;
-    src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), B.psi + (long long)k * n, n, M, A);
-    ++nl;
-    augment_x(B, A, M);
-    cudaMemsetAsync(L->XA, 0, sizeof(double) * n2 * M, st);
-    gram<T>(st, n, P(L->Xh), n, nullptr, n2, M, FPlain<T>{A, n, nullptr, M}, L->XA, n2, nl);
+    const T* A = Ain;
+    if (!A) {
+      src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), psi, n, Ms, P(L->Asrc));
+      ++nl;
+      A = P(L->Asrc);
+    }
+    augment_x(B, A, Ms);
+    cudaMemsetAsync(L->XA, 0, sizeof(double) * n2 * Ms, st);
+    gram<T>(st, n, P(L->Xh), n, nullptr, n2, Ms, FPlain<T>{A, n, nullptr, Ms}, L->XA, n2, nl);
     join();
-    launch_src_assemble<T>(st, B.S, RB, L->XA, Bk, P(L->Wh), m, M, n2, ctx->h, L->Sh);
+    launch_src_assemble<T>(st, B.S, RB, L->XA, Bk, P(L->Wh), m, Ms, n2, ctx->h, L->Sh);
     ++nl;
     launch_svd_truncate<T>(st, L->Sh, n2, RB, rank_params(), k, 1, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
                            ctx->dev_err);
@@ -693,6 +801,8 @@ struct Engine {
       for (size_t b = 0; b < bs.size(); ++b) {
         Beam<T>& B = bs[b];
         L = &ctx->lanes[b % nlanes];
+        if (ctx->ckpt_interval > 0 && k % ctx->ckpt_interval == 0)
+          snap_save(B, B.ckpt[k / ctx->ckpt_interval], L->s0);
         if (B.active) {
           streaming(B, k);
           scattering(B, k);
@@ -745,6 +855,7 @@ dlra_status alloc_shared(dlra_ctx* ctx) {
   ALLOC(ctx->tau_cell, sizeof(double) * n);
   ALLOC(ctx->Apm, sizeof(T) * (size_t)nk * m * m);
   ALLOC(ctx->dev_err, sizeof(int));
+  ALLOC(ctx->flags_dev, sizeof(int) * ctx->K);
   ALLOC(ctx->dose_tmp, sizeof(double) * n);
   return DLRA_OK;
 }
@@ -783,6 +894,104 @@ dlra_status alloc_lane(dlra_ctx* ctx) {
   return DLRA_OK;
 }
 
+RayGeo ray_geo(const dlra_ctx* ctx);
+
+template <typename T>
+dlra_status alloc_snap(dlra_ctx* ctx, Snap<T>& s) {
+  ALLOC(s.X, sizeof(T) * ctx->n * ctx->RB);
+  ALLOC(s.W, sizeof(T) * (size_t)ctx->m * ctx->RB);
+  ALLOC(s.S, sizeof(double) * ctx->RB * ctx->RB);
+  ALLOC(s.dims, sizeof(BeamDims));
+  return DLRA_OK;
+}
+
+// checkpoint slots of every beam for the current interval (before the first step)
+template <typename T>
+dlra_status ensure_checkpoints(dlra_ctx* ctx) {
+  const int I = ctx->ckpt_interval;
+  if (I <= 0) return DLRA_OK;
+  const size_t need = (size_t)((ctx->K + I - 1) / I);
+  for (auto& B : beams_of<T>(ctx))
+    while (B.ckpt.size() < need) {
+      B.ckpt.emplace_back();
+      dlra_status s = alloc_snap<T>(ctx, B.ckpt.back());
+      if (s != DLRA_OK) return s;
+    }
+  CK(cudaStreamSynchronize(ctx->st));
+  return DLRA_OK;
+}
+
+// work space of the reverse sweep; grows with the number of beams, sub-steps and rays
+template <typename T>
+dlra_status alloc_adj(dlra_ctx* ctx) {
+  const long long n = ctx->n;
+  const int m = ctx->m, RB = ctx->RB, K = ctx->K, M = ctx->M, N = ctx->N;
+  auto& bs = beams_of<T>(ctx);
+  const int nb = (int)bs.size();
+  if (!ctx->adj) ctx->adj = new AdjWork<T>();
+  AdjWork<T>& A = *reinterpret_cast<AdjWork<T>*>(ctx->adj);
+  if (!A.mu.X) {
+    for (Beam<T>* B : {&A.mu, &A.rep}) {
+      ALLOC(B->X, sizeof(T) * n * RB);
+      ALLOC(B->W, sizeof(T) * (size_t)m * RB);
+      ALLOC(B->S, sizeof(double) * RB * RB);
+      ALLOC(B->dims, sizeof(BeamDims));
+      ALLOC(B->rank_log, sizeof(int) * 2 * K);
+    }
+    dlra_status s = alloc_snap<T>(ctx, A.alpha);
+    if (s != DLRA_OK) return s;
+    ALLOC(A.gvec, sizeof(T) * n);
+    ALLOC(A.ge, sizeof(double) * n);
+    ALLOC(A.gtmp, sizeof(double) * n);
+    ALLOC(A.be0, sizeof(double) * m);
+    ALLOC(A.grad_rho, sizeof(double) * n);
+    ALLOC(A.grad_f, sizeof(double) * n);
+    ALLOC(A.grad_tau, sizeof(double) * n);
+    ALLOC(A.grad_w, sizeof(double) * M * n);
+    ALLOC(A.dw, sizeof(double) * M * n);
+    ALLOC(A.Cm, sizeof(double) * RB * RB);
+    ALLOC(A.Cl, sizeof(double) * (N + 1) * RB * RB);
+    ALLOC(A.ysrc, sizeof(double) * M * RB);
+    ALLOC(A.mcoef, sizeof(double) * 2 * M);
+    // the dose reads the l = 0 moment: e += h sqrt(4 pi) u(., 0)
+    const double s4 = std::sqrt(4.0 * M_PI);
+    CK(cudaMemcpyAsync(A.be0, &s4, sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  }
+  if (A.cap_ns < ctx->nsub_max) {
+    ALLOC(A.capf, sizeof(T) * (size_t)4 * ctx->nsub_max * n * RB);
+    ALLOC(A.capa, sizeof(T) * (size_t)4 * ctx->nsub_max * n * RB);
+    A.cap_ns = ctx->nsub_max;
+  }
+  while (A.seg.size() < (size_t)ctx->ckpt_interval * nb) {
+    A.seg.emplace_back();
+    dlra_status s = alloc_snap<T>(ctx, A.seg.back());
+    if (s != DLRA_OK) return s;
+  }
+  while ((int)A.gpsi.size() < nb) {
+    A.gpsi.push_back(nullptr);
+    ALLOC(A.gpsi.back(), sizeof(double) * (size_t)K * n);
+  }
+  if (nb > A.nb_cap) {
+    ALLOC(A.dbeta, sizeof(double) * nb);
+    A.nb_cap = nb;
+  }
+  size_t rb = 0;
+  RayGeo g = ray_geo(ctx);
+  for (int c : ctx->ray_count) rb = std::max(rb, raytrace_adjoint_scratch_bytes(c, g));
+  if (rb > A.ray_scratch_bytes) {
+    ALLOC(A.ray_scratch, rb);
+    A.ray_scratch_bytes = rb;
+  }
+  std::vector<double> mc(2 * M);
+  for (int i = 0; i < M; ++i) {
+    mc[2 * i] = ctx->mats[i].density * ctx->mats[i].sp_ratio;
+    mc[2 * i + 1] = ctx->tau_coef[i];
+  }
+  CK(cudaMemcpyAsync(A.mcoef, mc.data(), sizeof(double) * 2 * M, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return DLRA_OK;
+}
+
 template <typename T>
 dlra_status upload_apm(dlra_ctx* ctx) {
   // A^+_d = (A_d + |A_d|)/2 (s = 0) and A^-_d = (A_d - |A_d|)/2 (s = 1), row-major per k
@@ -809,6 +1018,7 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
   // mixture: S(x, E) = rho_s(x) S_w(E), rho_s = sum_i w_i rho_i s_i
   std::vector<double> rho_s(n, 0.0), rho(n, 0.0), tau(n, 0.0);
   std::vector<T> inv_rho(n), wc((size_t)M * n), wT((size_t)M * n);
+  ctx->tau_coef.assign(M, 0.0);
   for (int i = 0; i < M; ++i) {
     const dlra_material& mt = ctx->mats[i];
     double g0 = 0.0;
@@ -816,6 +1026,7 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
       const std::vector<double>& s = ctx->s_unit[i];
       g0 = (s[0] - (ctx->cfg.transport_correction ? s[ctx->N + 1] : 0.0)) / ctx->xi_unit[i];
     }
+    ctx->tau_coef[i] = mt.density * mt.scatter_ratio * g0;
     for (long long x = 0; x < n; ++x) {
       double wv = w_host[(size_t)i * n + x];
       rho_s[x] += wv * mt.density * mt.sp_ratio;
@@ -836,8 +1047,8 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
     }
   ctx->rho_s_host = rho_s;
   ctx->rho_host = rho;
-  ALLOC(ctx->wc, sizeof(T) * M * n);
-  ALLOC(ctx->wT, sizeof(T) * M * n);
+  if (!ctx->wc) ALLOC(ctx->wc, sizeof(T) * M * n);
+  if (!ctx->wT) ALLOC(ctx->wT, sizeof(T) * M * n);
   CK(cudaMemcpyAsync(ctx->inv_rho, inv_rho.data(), sizeof(T) * n, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->wc, wc.data(), sizeof(T) * wc.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->wT, wT.data(), sizeof(T) * wT.size(), cudaMemcpyHostToDevice, ctx->st));
@@ -872,8 +1083,11 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
       for (int l = 0; l <= ctx->N; ++l) coef[((size_t)k * M + i) * (ctx->N + 1) + l] = ctx->h * self[l] / Sw(ctx, E1);
     }
   }
-  ALLOC(ctx->sbeta, sizeof(double) * sbeta.size());
-  ALLOC(ctx->coef, sizeof(double) * coef.size());
+  if (ctx->sbeta_cap < sbeta.size()) {
+    ALLOC(ctx->sbeta, sizeof(double) * sbeta.size());
+    ctx->sbeta_cap = sbeta.size();
+  }
+  if (!ctx->coef) ALLOC(ctx->coef, sizeof(double) * coef.size());
   CK(cudaMemcpyAsync(ctx->sbeta, sbeta.data(), sizeof(double) * sbeta.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -889,6 +1103,24 @@ RayGeo ray_geo(const dlra_ctx* ctx) {
   g.klam = c.t100 * 1e4 * c.bk_p * c.bk_alpha / 2.0;
   g.volume = c.dx * c.dz * (ctx->two_d ? 1.0 : c.dy);
   return g;
+}
+
+// in-scattering moment vectors B[k][i][p] = G_{i,l(p)}(E_{k+1/2}) m_p(Omega) of one beam
+template <typename T>
+dlra_status upload_bsrc(dlra_ctx* ctx, Beam<T>& B) {
+  const int m = ctx->m, K = ctx->K, M = ctx->M;
+  std::vector<double> mo(m), Bh((size_t)K * M * m), self, src;
+  real_sh_dir(ctx->N, B.dir, mo.data());
+  for (int k = 0; k < K; ++k) {
+    double Em = 0.5 * (ctx->E[k] + ctx->E[k + 1]);
+    for (int i = 0; i < M; ++i) {
+      moments_at(ctx, i, Em, self, src);
+      for (int p = 0; p < m; ++p) Bh[((size_t)k * M + i) * m + p] = src[ctx->ang.degree[p]] * mo[p];
+    }
+  }
+  CK(cudaMemcpyAsync(B.Bsrc, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return DLRA_OK;
 }
 
 template <typename T>
@@ -967,7 +1199,7 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
   for (auto& pt : pts)
     for (size_t e = 0; e < ee.size(); ++e) {
       rays.insert(rays.end(), {pt.first[0], pt.first[1], pt.first[2], d[0], d[1], d[2], ee[e],
-                               b->weight * pt.second / wsum * ew[e]});
+                               pt.second / wsum * ew[e]});   // unit beam weight
     }
   const int nray = (int)(rays.size() / 8);
   if ((int)ctx->lanes.size() < ctx->max_lanes && ctx->lanes.size() <= beams_of<T>(ctx).size()) {
@@ -975,6 +1207,8 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
     if (ls != DLRA_OK) return ls;
   }
   Beam<T> B;
+  B.weight = b->weight;
+  for (int a = 0; a < 3; ++a) B.dir[a] = d[a];
   ALLOC(B.X, sizeof(T) * n * RB);
   ALLOC(B.W, sizeof(T) * (size_t)m * RB);
   ALLOC(B.S, sizeof(double) * RB * RB);
@@ -1002,18 +1236,12 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
   ++ctx->launches;
   B.has_src.assign(K, 0);
   CK(cudaMemcpyAsync(B.has_src.data(), flags, sizeof(int) * K, cudaMemcpyDeviceToHost, ctx->st));
-  // in-scattering moment vectors B[k][i][p] = G_{i,l(p)}(E_{k+1/2}) m_p(Omega)
-  std::vector<double> mo(m), Bh((size_t)K * M * m), self, src;
-  real_sh_dir(ctx->N, d, mo.data());
-  for (int k = 0; k < K; ++k) {
-    double Em = 0.5 * (ctx->E[k] + ctx->E[k + 1]);
-    for (int i = 0; i < M; ++i) {
-      moments_at(ctx, i, Em, self, src);
-      for (int p = 0; p < m; ++p) Bh[((size_t)k * M + i) * m + p] = src[ctx->ang.degree[p]] * mo[p];
-    }
-  }
-  CK(cudaMemcpyAsync(B.Bsrc, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  B.first_src = -1;
+  for (int k = 0; k < K && B.first_src < 0; ++k)
+    if (B.has_src[k]) B.first_src = k;
+  dlra_status us = upload_bsrc<T>(ctx, B);
+  if (us != DLRA_OK) return us;
   CK(cudaGetLastError());
   beams_of<T>(ctx).push_back(B);
   *id = (int32_t)beams_of<T>(ctx).size() - 1;
@@ -1082,7 +1310,8 @@ dlra_status dose_t(dlra_ctx* ctx, double* out, int on_device, int per_mass) {
   double* dst = on_device ? out : ctx->dose_tmp;
   if (bs.empty()) CK(cudaMemsetAsync(dst, 0, sizeof(double) * n, ctx->st));
   for (size_t b = 0; b < bs.size(); ++b)
-    dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[b].e_c, bs[b].e_u, n, b == 0 ? 1 : 0, dst);
+    dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[b].e_c, bs[b].e_u, n, b == 0 ? 1 : 0, bs[b].weight,
+                                                         dst);
   if (per_mass) div_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(dst, ctx->rho, n);
   CK(cudaGetLastError());
   if (!on_device) {
@@ -1093,12 +1322,15 @@ dlra_status dose_t(dlra_ctx* ctx, double* out, int on_device, int per_mass) {
 }
 
 template <typename T>
-dlra_status reset_t(dlra_ctx* ctx, int retrace) {
+dlra_status reset_t(dlra_ctx* ctx, int retrace, bool flags_changed = false) {
   const long long n = ctx->n;
   auto& bs = beams_of<T>(ctx);
   RayGeo g = ray_geo(ctx);
   for (size_t b = 0; b < bs.size(); ++b) {
     Beam<T>& B = bs[b];
+    // the factors too: kernels read all rank_max columns and rely on those beyond the rank being zero
+    CK(cudaMemsetAsync(B.X, 0, sizeof(T) * n * ctx->RB, ctx->st));
+    CK(cudaMemsetAsync(B.W, 0, sizeof(T) * (size_t)ctx->m * ctx->RB, ctx->st));
     CK(cudaMemsetAsync(B.dims, 0, sizeof(BeamDims), ctx->st));
     CK(cudaMemsetAsync(B.e_c, 0, sizeof(double) * n, ctx->st));
     CK(cudaMemsetAsync(B.S, 0, sizeof(double) * ctx->RB * ctx->RB, ctx->st));
@@ -1108,11 +1340,141 @@ dlra_status reset_t(dlra_ctx* ctx, int retrace) {
       CK(cudaMemsetAsync(B.e_u, 0, sizeof(double) * n, ctx->st));
       launch_raytrace(ctx->st, ctx->ray_dev[b], ctx->ray_count[b], g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
       ++ctx->launches;
+      if (flags_changed) {
+        // the mixture changed: the bins the beam reaches may have changed too
+        CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(int) * ctx->K, ctx->st));
+        bin_flags_kernel<<<dim3(std::min<unsigned>(nblk(n, 256), 64), ctx->K), 256, 0, ctx->st>>>(B.psi, n, ctx->K,
+                                                                                                  ctx->flags_dev);
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(B.has_src.data(), ctx->flags_dev, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        B.first_src = -1;
+        for (int k = 0; k < ctx->K && B.first_src < 0; ++k)
+          if (B.has_src[k]) B.first_src = k;
+      }
     }
     B.active = false;
   }
   CK(cudaGetLastError());
   ctx->step = 0;
+  return DLRA_OK;
+}
+
+// Reverse sweep (discrete adjoint) of the ctx->step energy steps run so far, for the loss
+// gradient dL/de already in the work space (ge, gvec). Segment by segment from the last
+// checkpoint: replay the forward steps of the segment, storing every step's start state;
+// then, step by step backwards, advance the adjoint state mu through the transposed step
+// (dose source, collision, streaming) and pair it with the replayed forward quantities.
+template <typename T>
+dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int out_on_device) {
+  Engine<T> E{ctx};
+  AdjWork<T>& A = *reinterpret_cast<AdjWork<T>*>(ctx->adj);
+  auto& bs = E.beams();
+  const int nb = (int)bs.size();
+  const long long n = ctx->n;
+  const int RB = ctx->RB, m = ctx->m, M = ctx->M, N = ctx->N;
+  const int Kp = ctx->step, I = ctx->ckpt_interval;
+  E.L = &ctx->lanes[0];
+  cudaStream_t st = E.L->s0;
+  int64_t& nl = ctx->launches;
+  cudaEventRecord(ctx->ev_step, ctx->st);
+  cudaStreamWaitEvent(st, ctx->ev_step, 0);
+  // dL/dbeta_b = <dL/de, e_c,b + e_u,b>: the deposit is linear in each beam weight
+  cudaMemsetAsync(A.dbeta, 0, sizeof(double) * nb, st);
+  for (int b = 0; b < nb; ++b) {
+    launch_dot(st, A.ge, bs[b].e_c, bs[b].e_u, n, A.dbeta + b);
+    ++nl;
+  }
+  cudaMemsetAsync(A.grad_rho, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(A.grad_f, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(A.grad_tau, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(A.grad_w, 0, sizeof(double) * M * n, st);
+  for (int b = 0; b < nb; ++b) cudaMemsetAsync(A.gpsi[b], 0, sizeof(double) * (size_t)ctx->K * n, st);
+  convert_kernel<T><<<nblk(n, 256), 256, 0, st>>>(A.ge, A.gvec, n);
+  ++nl;
+  cudaMemsetAsync(A.mu.X, 0, sizeof(T) * n * RB, st);
+  cudaMemsetAsync(A.mu.W, 0, sizeof(T) * (size_t)m * RB, st);
+  cudaMemsetAsync(A.mu.S, 0, sizeof(double) * RB * RB, st);
+  cudaMemsetAsync(A.mu.dims, 0, sizeof(BeamDims), st);
+  auto active_at = [&](int b, int k) { return bs[b].first_src >= 0 && k > bs[b].first_src; };
+  const int nseg = (Kp + I - 1) / I;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * I, k1 = std::min(Kp, k0 + I);
+    // replay the segment from its checkpoint
+    for (int b = 0; b < nb; ++b) {
+      Beam<T>& B = bs[b];
+      E.snap_load(B.ckpt[sg], A.rep, st);
+      for (int k = k0; k < k1; ++k) {
+        E.snap_save(A.rep, A.seg[(size_t)(k - k0) * nb + b], st);
+        if (k + 1 == k1) break;
+        if (active_at(b, k)) {
+          E.streaming(A.rep, k);
+          E.scattering(A.rep, k);
+        }
+        if (B.has_src[k]) E.source_with(A.rep, k, nullptr, B.Bsrc + (long long)k * M * m, M, B.psi + (long long)k * n);
+      }
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      // dose: e += h sqrt(4 pi) u_{k+1}(., 0) gives mu += h sqrt(4 pi) dL/de e_0^T
+      E.adj_rank = true;
+      E.source_with(A.mu, k, A.gvec, A.be0, 1, nullptr);
+      E.adj_rank = false;
+      // first-collision source of each beam: u_{k+1} += h beta_b sum_i diag(w_i psi_b) 1 B_i^T
+      for (int b = 0; b < nb; ++b) {
+        Beam<T>& B = bs[b];
+        if (!B.has_src[k]) continue;
+        launch_grad_source<T>(st, A.mu.X, A.mu.S, A.mu.W, n, m, RB, B.Bsrc + (long long)k * M * m, M,
+                              B.psi + (long long)k * n, E.P(ctx->wT), B.weight * ctx->h, A.ysrc, A.grad_w,
+                              A.gpsi[b] + (long long)k * n);
+        nl += 2;
+      }
+      bool any = false;
+      for (int b = 0; b < nb; ++b) any = any || active_at(b, k);
+      if (!any) continue;
+      // transposed collision (the implicit factor 1/(1 - F) is diagonal, hence self-adjoint)
+      // and transposed streaming with the adjoints of the K-stage inputs captured
+      E.adj_rank = true;
+      E.scattering(A.mu, k);
+      E.snap_save(A.mu, A.alpha, st);
+      E.streaming(A.mu, k, 1, A.capa);
+      E.adj_rank = false;
+      const int ns = ctx->nsub[k];
+      for (int b = 0; b < nb; ++b) {
+        if (!active_at(b, k)) continue;
+        Beam<T>& B = bs[b];
+        E.snap_load(A.seg[(size_t)(k - k0) * nb + b], A.rep, st);
+        // C = W_f^T W_alpha: the forward K-step basis against the adjoint K-step basis
+        cudaMemsetAsync(A.Cm, 0, sizeof(double) * RB * RB, st);
+        gram<T>(st, m, A.rep.W, m, nullptr, RB, RB, FPlain<T>{A.alpha.W, m, nullptr, RB}, A.Cm, RB, nl);
+        E.streaming(A.rep, k, 0, A.capf);
+        E.scattering(A.rep, k);
+        launch_grad_stream<T>(st, A.capf, A.capa, 4 * ns, n, RB, A.Cm, B.weight, A.grad_rho);
+        launch_scatter_cl(st, A.alpha.S, A.alpha.W, A.rep.S, A.rep.W, sizeof(T) == 8 ? 1 : 0, m, N, RB, A.Cl);
+        launch_grad_scatter<T>(st, A.alpha.X, A.rep.X, n, RB, A.Cl, N, ctx->coef + (long long)k * M * (N + 1), M,
+                               E.P(ctx->wc), ctx->f_cell, B.weight, A.grad_w, A.grad_rho);
+        nl += 3;
+      }
+    }
+  }
+  // uncollided part: the ray tracer's reverse walk with dL/dpsi_b and dL/de_u,b = beta_b dL/de
+  RayGeo g = ray_geo(ctx);
+  for (int b = 0; b < nb; ++b) {
+    scale_kernel<<<nblk(n, 256), 256, 0, st>>>(A.ge, bs[b].weight, n, A.gtmp);
+    launch_raytrace_adjoint(st, ctx->ray_dev[b], ctx->ray_count[b], g, ctx->f_cell, ctx->tau_cell, A.gpsi[b], A.gtmp,
+                            A.ray_scratch, A.grad_f, A.grad_tau);
+    nl += 2;
+  }
+  double* dst = (dw_out && out_on_device) ? dw_out : A.dw;
+  launch_grad_assemble(st, A.grad_w, A.grad_rho, A.grad_f, A.grad_tau, A.mcoef, M, n, dst);
+  ++nl;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, DLRA_ERR_CUDA, "reverse sweep launch failed: %s", cudaGetErrorString(e));
+  cudaEventRecord(E.L->ev[2], st);
+  cudaStreamWaitEvent(ctx->st, E.L->ev[2], 0);
+  if (dw_out && !out_on_device)
+    CK(cudaMemcpyAsync(dw_out, A.dw, sizeof(double) * M * n, cudaMemcpyDeviceToHost, ctx->st));
+  if (dbeta_host) CK(cudaMemcpyAsync(dbeta_host, A.dbeta, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   return DLRA_OK;
 }
 
@@ -1335,7 +1697,8 @@ dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material
                                int32_t w_on_device) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "materials already set");
+  if (ctx->materials_set && n_mat != ctx->M)
+    return fail(ctx, DLRA_ERR_STATE, "materials can be replaced only with the same number (%d)", ctx->M);
   if (n_mat < 1 || !mats || !w) return fail(ctx, DLRA_ERR_ARG, "need n_mat >= 1, mats and w");
   if (n_mat > ctx->RB) return fail(ctx, DLRA_ERR_ARG, "n_mat must not exceed the rank capacity");
   for (int i = 0; i < n_mat; ++i) {
@@ -1357,9 +1720,87 @@ dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material
   }
   for (size_t i = 0; i < (size_t)n_mat * ctx->n; ++i)
     if (!(w_host[i] >= 0.0) || std::isinf(w_host[i])) return fail(ctx, DLRA_ERR_ARG, "mixture weights must be finite and >= 0");
+  const bool again = ctx->materials_set;
   dlra_status s = ctx->fp64 ? set_materials_t<double>(ctx, w_host) : set_materials_t<float>(ctx, w_host);
-  if (s == DLRA_OK) ctx->materials_set = true;
+  if (s != DLRA_OK) return s;
+  ctx->materials_set = true;
+  if (again) {
+    // new mixture: new in-scattering vectors, ray trace and source bins; every beam restarts
+    if (ctx->fp64) {
+      for (auto& B : beams_of<double>(ctx))
+        if ((s = upload_bsrc<double>(ctx, B)) != DLRA_OK) return s;
+      s = reset_t<double>(ctx, 1, true);
+    } else {
+      for (auto& B : beams_of<float>(ctx))
+        if ((s = upload_bsrc<float>(ctx, B)) != DLRA_OK) return s;
+      s = reset_t<float>(ctx, 1, true);
+    }
+  }
   return s;
+}
+
+dlra_status dlra_set_beam_weight(dlra_ctx* ctx, int32_t beam_id, double weight) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  if (beam_id < 0 || (size_t)beam_id >= nb) return fail(ctx, DLRA_ERR_ARG, "bad beam id");
+  if (!(weight >= 0.0) || std::isinf(weight)) return fail(ctx, DLRA_ERR_ARG, "beam weight must be finite and >= 0");
+  if (ctx->fp64) beams_of<double>(ctx)[beam_id].weight = weight;
+  else beams_of<float>(ctx)[beam_id].weight = weight;
+  return DLRA_OK;
+}
+
+dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (checkpoint_interval < 0) return fail(ctx, DLRA_ERR_ARG, "checkpoint_interval must be >= 0");
+  if (ctx->step != 0) return fail(ctx, DLRA_ERR_STATE, "the reverse sweep must be enabled before the first step");
+  if (checkpoint_interval != ctx->ckpt_interval) {
+    if (ctx->fp64) for (auto& B : beams_of<double>(ctx)) B.ckpt.clear();
+    else for (auto& B : beams_of<float>(ctx)) B.ckpt.clear();
+  }
+  ctx->ckpt_interval = checkpoint_interval;
+  return DLRA_OK;
+}
+
+dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
+                          double* dL_dw, int32_t out_on_device) {
+  if (!ctx) return DLRA_ERR_ARG;
+  dlra_status s = check_device_errors(ctx);
+  if (s != DLRA_OK) return s;
+  if (!dL_de) return fail(ctx, DLRA_ERR_ARG, "null dL_de");
+  if (!ctx->materials_set) return fail(ctx, DLRA_ERR_STATE, "no materials");
+  if (ctx->ckpt_interval <= 0) return fail(ctx, DLRA_ERR_STATE, "dlra_enable_adjoint was not called before stepping");
+  if (ctx->step == 0) return fail(ctx, DLRA_ERR_STATE, "no energy step to differentiate");
+  const size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
+  const long long n = ctx->n;
+  std::vector<double> gh(n);
+  if (in_on_device) CK(cudaMemcpy(gh.data(), dL_de, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  else std::memcpy(gh.data(), dL_de, sizeof(double) * n);
+  bool zero = true;
+  for (double v : gh) {
+    if (!std::isfinite(v)) return fail(ctx, DLRA_ERR_ARG, "dL_de must be finite");
+    zero = zero && v == 0.0;
+  }
+  s = ctx->fp64 ? alloc_adj<double>(ctx) : alloc_adj<float>(ctx);
+  if (s != DLRA_OK) return s;
+  const size_t Mn = (size_t)ctx->M * n;
+  if (zero) {
+    // a zero loss gradient has zero gradients (and an adjoint state of rank 0)
+    if (dL_dweight) std::fill(dL_dweight, dL_dweight + nb, 0.0);
+    if (dL_dw) {
+      if (out_on_device) CK(cudaMemset(dL_dw, 0, sizeof(double) * Mn));
+      else std::fill(dL_dw, dL_dw + Mn, 0.0);
+    }
+    return DLRA_OK;
+  }
+  double* ge = ctx->fp64 ? reinterpret_cast<AdjWork<double>*>(ctx->adj)->ge
+                         : reinterpret_cast<AdjWork<float>*>(ctx->adj)->ge;
+  CK(cudaMemcpyAsync(ge, gh.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  s = ctx->fp64 ? backward_t<double>(ctx, dL_dweight, dL_dw, out_on_device)
+                : backward_t<float>(ctx, dL_dweight, dL_dw, out_on_device);
+  if (s != DLRA_OK) return s;
+  return check_device_errors(ctx);
 }
 
 dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id) {
@@ -1381,6 +1822,10 @@ dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
   size_t nb = ctx->fp64 ? beams_of<double>(ctx).size() : beams_of<float>(ctx).size();
   if (nb == 0) return fail(ctx, DLRA_ERR_STATE, "no beam added");
   if (ctx->step + n_steps > ctx->K) return fail(ctx, DLRA_ERR_STATE, "only %d energy steps remain", ctx->K - ctx->step);
+  if (ctx->ckpt_interval > 0) {
+    dlra_status s = ctx->fp64 ? ensure_checkpoints<double>(ctx) : ensure_checkpoints<float>(ctx);
+    if (s != DLRA_OK) return s;
+  }
   return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
 }
 
@@ -1539,6 +1984,10 @@ void dlra_destroy(dlra_ctx* ctx) {
   if (ctx->beams) {
     if (ctx->fp64) free_beams<double>(ctx);
     else free_beams<float>(ctx);
+  }
+  if (ctx->adj) {
+    if (ctx->fp64) delete reinterpret_cast<AdjWork<double>*>(ctx->adj);
+    else delete reinterpret_cast<AdjWork<float>*>(ctx->adj);
   }
   delete ctx;
 }

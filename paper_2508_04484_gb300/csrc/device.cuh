@@ -390,6 +390,8 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
                                                      const int* __restrict__ rdim, T beta, int last) {
   // vin = rho^-1 z (scaled stage input). last = 0: vout = rho^-1 (y + beta acc);
   // last = 1: yout = y + beta acc and vout = rho^-1 yout (input of the next sub-step).
+  // last = 2 (transposed operator, unscaled input; Pst holds -P of the opposite sign):
+  // vout = beta rho^-1 acc and yout = y + vout (y may alias yout, never vin).
   constexpr int NK = 2 * NACT;
   constexpr int NP = 1 + 4 * NACT;
   extern __shared__ __align__(16) unsigned char raw[];
@@ -455,7 +457,14 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
     }
   }
   const T ir0 = inv_rho[i];
-  if (last) {
+  if (last == 2) {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      const T lam = beta * ir0 * acc[c];
+      vout[(long long)c * ld + i] = lam;
+      yout[(long long)c * ld + i] = y[(long long)c * ld + i] + lam;
+    }
+  } else if (last) {
 #pragma unroll
     for (int c = 0; c < RM; ++c) {
       const T yn = y[(long long)c * ld + i] + beta * acc[c];

@@ -76,6 +76,41 @@ struct RayGeo {
 void launch_raytrace(cudaStream_t st, const double* rays, int nray, RayGeo g, const double* f_cell,
                      const double* tau_cell, double* psi, double* e_u);
 
+// Reverse-mode derivative of the ray tracer: for adjoint seeds gpsi (K x n) and geu (n),
+// adds dL/df(x) and dL/dtau(x) (stopping factor, removal factor) to grad_f and grad_tau.
+// scratch: raytrace_adjoint_scratch_bytes (the recorded voxel segments of every ray).
+size_t raytrace_adjoint_scratch_bytes(int nray, RayGeo g);
+void launch_raytrace_adjoint(cudaStream_t st, const double* rays, int nray, RayGeo g, const double* f_cell,
+                             const double* tau_cell, const double* gpsi, const double* geu, void* scratch,
+                             double* grad_f, double* grad_tau);
+
+// Gradient kernels of the reverse sweep (adjoint.cu). Tall arrays n x RB, ld n; RB is a
+// compiled rank capacity.
+// grad_rho -= coef sum_q vq_q C lq_q^T row by row (nq stage pairs, stride n RB; C RB x RB).
+template <typename T>
+void launch_grad_stream(cudaStream_t st, const T* vq, const T* lq, int nq, long long n, int RB, const double* C,
+                        double coef, double* grad_rho);
+// Cl[l] = Sa (Wa[l]^T Wb[l]) Sb^T per degree l = 0..N (W of type float or double).
+void launch_scatter_cl(cudaStream_t st, const double* Sa, const void* Wa, const double* Sb, const void* Wb, int fp64,
+                       int m, int N, int RB, double* Cl);
+// dL/dw_i and dL/d rho_s of the implicit scattering factor from D(x, l) = Xa(x,:) Cl[l] Xb(x,:)^T.
+template <typename T>
+void launch_grad_scatter(cudaStream_t st, const T* Xa, const T* Xb, long long n, int RB, const double* Cl, int N,
+                         const double* coef, int M, const T* wc, const double* rho_s, double beta, double* grad_w,
+                         double* grad_rho);
+// Source term of one beam: dL/dw_i += bh psi mu.B_i and gpsi = bh sum_i w_i mu.B_i, mu = X S W^T.
+template <typename T>
+void launch_grad_source(cudaStream_t st, const T* X, const double* S, const T* W, long long n, int m, int RB,
+                        const double* B, int M, const double* psi, const T* w, double bh, double* ysrc,
+                        double* grad_w, double* gpsi);
+// out[i][x] = grad_w[i][x] + mcoef[2i] (grad_rho + grad_f)[x] + mcoef[2i+1] grad_tau[x]
+void launch_grad_assemble(cudaStream_t st, const double* grad_w, const double* grad_rho, const double* grad_f,
+                          const double* grad_tau, const double* mcoef, int M, long long n, double* out);
+// *out += sum_x g[x] (a[x] + b[x])
+void launch_dot(cudaStream_t st, const double* g, const double* a, const double* b, long long n, double* out);
+// transpose each of nk column-major n2 x n2 blocks in place
+void launch_transpose_blocks(cudaStream_t st, double* G, int n2, int nk);
+
 // Work-space bytes of one stand-alone K-step (see dlra_kstep) and the step itself on
 // caller-provided device work space of at least that many bytes.
 size_t kstep_scratch_bytes(long long n, int r, int nact);

@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdlra.so")
 
 DLRA_OK = 0
+(DLRA_ERR_ARG, DLRA_ERR_STATE, DLRA_ERR_CUDA, DLRA_ERR_OOM, DLRA_ERR_NONFINITE, DLRA_ERR_RANK,
+ DLRA_ERR_TIMEOUT) = range(1, 8)
 STATUS = {0: "DLRA_OK", 1: "DLRA_ERR_ARG", 2: "DLRA_ERR_STATE", 3: "DLRA_ERR_CUDA", 4: "DLRA_ERR_OOM",
           5: "DLRA_ERR_NONFINITE", 6: "DLRA_ERR_RANK", 7: "DLRA_ERR_TIMEOUT"}
 FOKKER_PLANCK, BOLTZMANN = 0, 1
@@ -79,6 +81,9 @@ SIGNATURES = {
     "dlra_get_tables": ([_P, _DP, _DP], C.c_int),
     "dlra_get_substeps": ([_P, _IP], C.c_int),
     "dlra_reset": ([_P, C.c_int32], C.c_int),
+    "dlra_set_beam_weight": ([_P, C.c_int32, C.c_double], C.c_int),
+    "dlra_enable_adjoint": ([_P, C.c_int32], C.c_int),
+    "dlra_backward": ([_P, _P, C.c_int32, _DP, _P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
@@ -285,6 +290,33 @@ def dlra_reset(ctx, retrace=True):
     _check(ctx, load().dlra_reset(ctx, int(bool(retrace))))
 
 
+def dlra_set_beam_weight(ctx, beam_id: int, weight: float):
+    _check(ctx, load().dlra_set_beam_weight(ctx, int(beam_id), float(weight)))
+
+
+def dlra_enable_adjoint(ctx, checkpoint_interval: int = 16):
+    _check(ctx, load().dlra_enable_adjoint(ctx, int(checkpoint_interval)))
+
+
+def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
+    """Reverse sweep: returns (dL/dweight (n_beams,) numpy, dL/dw (n_mat, n)).
+
+    ``dL_de``: numpy float64 (n,) or a CUDA float64 tensor. dL/dw is written into
+    ``dw_out`` (CUDA float64 tensor of n_mat * n) when given, else returned as numpy."""
+    dbeta = np.zeros(max(n_beams, 1))
+    if _is_cuda_tensor(dL_de):
+        gin, gdev = C.c_void_p(dL_de.data_ptr()), 1
+    else:
+        g = np.ascontiguousarray(np.asarray(dL_de, dtype=np.float64).reshape(-1))
+        gin, gdev = g.ctypes.data_as(C.c_void_p), 0
+    if dw_out is not None and _is_cuda_tensor(dw_out):
+        _check(ctx, load().dlra_backward(ctx, gin, gdev, _dptr(dbeta), C.c_void_p(dw_out.data_ptr()), 1))
+        return dbeta[:n_beams], dw_out
+    dw = np.zeros((n_mat, n))
+    _check(ctx, load().dlra_backward(ctx, gin, gdev, _dptr(dbeta), dw.ctypes.data_as(C.c_void_p), 0))
+    return dbeta[:n_beams], dw
+
+
 def dlra_set_profiling(ctx, enable=True):
     _check(ctx, load().dlra_set_profiling(ctx, int(bool(enable))))
 
@@ -362,7 +394,19 @@ class Solver:
             self.add_beam(b)
 
     def set_materials(self, materials, w):
+        """Set (or replace, same number of materials) the mixture; replacing retraces and rewinds."""
+        self.n_mat = len(materials)
         dlra_set_materials(self.ctx, materials, w)
+
+    def set_beam_weight(self, beam_id, weight):
+        dlra_set_beam_weight(self.ctx, beam_id, weight)
+
+    def enable_adjoint(self, checkpoint_interval=16):
+        dlra_enable_adjoint(self.ctx, checkpoint_interval)
+
+    def backward(self, dL_de, dw_out=None):
+        """(dL/dweight per beam, dL/dw per material and cell) of a loss of the dose."""
+        return dlra_backward(self.ctx, dL_de, len(self.beam_ids), self.n_mat, self.n, dw_out)
 
     def add_beam(self, beam):
         self.beam_ids.append(dlra_add_beam(self.ctx, beam))
@@ -429,3 +473,40 @@ class Solver:
                 self.close()
         except Exception:
             pass
+
+
+_DOSE_FN = None
+
+
+def differentiable_dose(solver: "Solver", materials, w, weights):
+    """Dose e (CUDA float64, n) as a differentiable function of the mixture weights
+    ``w`` (CUDA float64 tensor (n_mat, n)) and the beam weights ``weights`` (float64
+    tensor (n_beams,)). The forward replaces the mixture (which retraces and rewinds
+    every beam), sets the beam weights and runs all energy steps; the backward is the
+    library's reverse sweep (``solver.enable_adjoint`` must have been called)."""
+    global _DOSE_FN
+    import torch
+
+    if _DOSE_FN is None:
+        class _DoseFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, solver_, materials_, w_, weights_):
+                solver_.set_materials(materials_, w_.detach().contiguous())
+                for b, wt in enumerate(weights_.detach().cpu().tolist()):
+                    solver_.set_beam_weight(b, wt)
+                solver_.step(solver_.K)
+                e = torch.empty(solver_.n, dtype=torch.float64, device=w_.device)
+                solver_.dose(out=e)
+                fctx.solver = solver_
+                fctx.wdev = weights_.device
+                return e
+
+            @staticmethod
+            def backward(fctx, grad_e):
+                sv = fctx.solver
+                dw = torch.empty((sv.n_mat, sv.n), dtype=torch.float64, device=grad_e.device)
+                dbeta, _ = sv.backward(grad_e.detach().to(torch.float64).contiguous(), dw_out=dw)
+                return None, None, dw, torch.as_tensor(dbeta, dtype=torch.float64, device=fctx.wdev)
+
+        _DOSE_FN = _DoseFunction
+    return _DOSE_FN.apply(solver, materials, w, weights)

@@ -117,6 +117,22 @@ def test_slab_run_matches_oracle(precision, tol):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(WL.FP64, 1e-5), (WL.FP32_MIXED, 1e-3)])
+def test_rewound_solve_matches_oracle(precision, tol):
+    # a solve after dlra_reset (how the bench repeats solves) must equal the first one
+    cfg, mats, w, beams = _slab(precision=precision)
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    dose, res = oracle_dlra(prob, src, OP.FIXED, rank=6)
+    s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=precision)
+    d1 = s.run()
+    s.reset(retrace=True)
+    d2 = s.run()
+    assert rel_l2(d2, d1) < (1e-12 if precision == WL.FP64 else 1e-5)
+    assert rel_l2(d2, dose) < tol
+    s.close()
+
+
 def test_heterogeneous_cube_fp32_matches_oracle():
     cfg, mats, w, beams = _cube()
     prob = oracle_problem(cfg, mats, w)

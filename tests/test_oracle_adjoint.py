@@ -133,3 +133,51 @@ def test_gradient_matches_finite_differences_3d():
     for i, x in [(0, cells[1]), (1, cells[2]), (0, cells[-1]), (1, 0)]:
         fd = AD.finite_difference(fac, beams, w, loss, i, x)
         assert abs(g["dw"][i, x] - fd) < 2e-5 * abs(fd) + 1e-6, (i, x, g["dw"][i, x], fd)
+
+
+def test_low_rank_sweep_one_step_is_exact():
+    from oracle import dlra as DL
+    from oracle import dlra_adjoint as LA
+    cfg, mats, w, fac, rng = _case(K=1)
+    beams = [dict(energy=60.0, pos=[0.7, 0, 0], dir=[0.3, 0, 1], spot_sigma=0.0, weight=0.8),
+             dict(energy=55.0, pos=[1.0, 0, 0], dir=[-0.2, 0, 1], spot_sigma=0.1, weight=1.3)]
+    g = rng.standard_normal(w.shape[1])
+    ref = AD.gradient(fac(w), beams, g)
+    lr = LA.gradient(fac(w), beams, g, DL.RankControl(mode=P.ADAPTIVE, tol=1e-12, r_max=16))
+    assert np.linalg.norm(lr["dw"] - ref["dw"]) < 1e-12 * np.linalg.norm(ref["dw"])
+    assert np.linalg.norm(lr["dbeta"] - ref["dbeta"]) < 1e-12 * np.linalg.norm(ref["dbeta"])
+
+
+def test_horner_k_step_equals_classic_rk4():
+    from oracle import dlra as DL
+    from oracle import dlra_adjoint as LA
+    cfg, mats, w, fac, rng = _case(K=3)
+    prob = fac(w)
+    X, _ = np.linalg.qr(rng.standard_normal((prob.n, 5)))
+    W, _ = np.linalg.qr(rng.standard_normal((prob.m, 5)))
+    S = np.diag([3.0, 2.0, 1.0, 0.5, 0.2])
+    K1 = DL.streaming_bug(prob, X, S, W, 1)[3]
+    K1h, v = LA.kstep(prob, X, S, W, 1, False)
+    assert np.abs(K1h - K1).max() < 1e-12 * np.abs(K1).max()
+    assert len(v) == 4 * prob.n_sub(1)
+    # the transposed K-step is the transpose of the forward map: <Y, K(X0)> = <K^T(Y), X0> in the W basis
+    Y, _ = np.linalg.qr(rng.standard_normal((prob.n, 5)))
+    Kt, _ = LA.kstep(prob, Y, np.eye(5), W, 1, True)
+    assert abs(np.sum(Y * K1h) - np.sum(Kt * (X @ S))) < 1e-11 * abs(np.sum(Y * K1h))
+
+
+def test_low_rank_sweep_converges_to_the_full_rank_gradient():
+    from oracle import dlra as DL
+    from oracle import dlra_adjoint as LA
+    errs = []
+    for K in (6, 24):
+        cfg, mats, w, fac, rng = _case(nx=8, nz=8, K=K, seed=2)
+        x = (np.arange(8) + 0.5) * 0.25
+        Xg, Zg = np.meshgrid(x, x)
+        g = np.exp(-((Xg - 1.2) ** 2 + (Zg - 1.0) ** 2) / 0.5).ravel()
+        beams = [dict(energy=60.0, pos=[1.1, 0, 0], dir=[0.2, 0, 1], spot_sigma=0.1, weight=1.0)]
+        ref = AD.gradient(fac(w), beams, g)
+        lr = LA.gradient(fac(w), beams, g, DL.RankControl(mode=P.ADAPTIVE, tol=1e-6, r_max=16))
+        errs.append(np.linalg.norm(lr["dw"] - ref["dw"]) / np.linalg.norm(ref["dw"]))
+    assert errs[1] < 0.2 * errs[0], errs
+    assert errs[1] < 1e-2, errs
