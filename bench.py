@@ -43,6 +43,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--energy-steps", type=int, default=0,
                    help="profiling only: stop each solve after this many energy steps")
     p.add_argument("--workload", default=WORKLOAD,
@@ -357,6 +358,33 @@ def main():
                "d2h_bytes_per_step": int(dose_host.nbytes),
                "includes": "context creation with angular tables, host->device mixture weights, ray trace, "
                            "all energy steps, dose read back to host"}
+    # ---- reverse sweep (gradients of L = |e|^2 / 2 w.r.t. beam and mixture weights), outside the timed region ----
+    adj = None
+    if rank == 0 and ws == 1 and not args.no_adjoint:
+        interval = 16
+        s3 = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
+        s3.enable_adjoint(interval)
+        g_dev = torch.zeros(n, dtype=torch.float64, device=dev)
+        dw_dev = torch.empty((len(mats), n), dtype=torch.float64, device=dev)
+        fwd, bwd = [], []
+        for _ in range(2):
+            s3.reset(retrace=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s3.step(K)
+            s3.dose(out=g_dev)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s3.backward(g_dev, dw_out=dw_dev)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            fwd.append(t1 - t0)
+            bwd.append(t2 - t1)
+        s3.close()
+        adj = {"ms_per_backward": 1000.0 * min(bwd), "ms_forward_with_checkpoints": 1000.0 * min(fwd),
+               "backward_over_forward": min(bwd) / (ms_per_solve / 1000.0), "checkpoint_interval": interval,
+               "loss": "|e|^2/2 (dL/de = e)", "outputs": "dL/dweight per beam, dL/dw per material and cell",
+               "timing": "host wall clock around synchronising calls, best of two passes"}
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cfg_c, mats_c, w_c, beams_c = _workload()
@@ -374,7 +402,7 @@ def main():
                 "energy_steps_per_s": value,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": vs_plain}
+                "vs_plain": vs_plain, "adjoint": adj}
         if args.workload != WORKLOAD:
             line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
                               "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,
