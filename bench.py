@@ -44,6 +44,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
+    p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
+                   help="replay the energy steps from CUDA graphs (auto: on for multi-beam workloads)")
     p.add_argument("--energy-steps", type=int, default=0,
                    help="profiling only: stop each solve after this many energy steps")
     p.add_argument("--workload", default=WORKLOAD,
@@ -177,14 +179,16 @@ def cpu_baseline(cfg, mats, w, beams, budget_steps=4):
                       f"{dt:.1f} s, numpy/BLAS threads on {cores} cores"}
 
 
-def _solve_ms(cfg, mats, w, beams, K, lanes, reps):
-    """Mean device time (ms) of one whole solve with the given number of lanes."""
+def _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=False):
+    """Mean device time (ms) of one whole solve with the given number of lanes (graphs: the
+    energy steps replayed from a CUDA graph captured on the first, untimed solve)."""
     import torch
     from paper_2508_04484_gb300 import dlra as D
     stream = torch.cuda.Stream()
     s = D.Solver(dict(cfg, max_concurrent_beams=lanes), mats, w, beams, stream=stream.cuda_stream)
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     dose = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.set_graphs(graphs)
     times = []
     for i in range(reps + 1):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -205,10 +209,13 @@ def _plain_vs_batched(cfg, mats, w, beams, K, args):
     """The same multi-beam solve with one beam after the other (one lane) and with the
     beams advanced concurrently (one lane per beam)."""
     reps = max(1, min(args.steps, 3))
+    lanes = min(len(beams), 32)
     plain = _solve_ms(cfg, mats, w, beams, K, 1, reps)
-    batched = _solve_ms(cfg, mats, w, beams, K, min(len(beams), 32), reps)
-    return {"plain_ms_per_solve": plain, "batched_ms_per_solve": batched, "speedup": plain / batched,
-            "beams": len(beams), "lanes": min(len(beams), 32)}
+    direct = _solve_ms(cfg, mats, w, beams, K, lanes, reps)
+    graph = _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=True)
+    return {"plain_ms_per_solve": plain, "batched_ms_per_solve": graph, "speedup": plain / graph,
+            "batched_direct_launch_ms_per_solve": direct, "beams": len(beams), "lanes": lanes,
+            "batched": "one lane (work space + stream pair) per beam, energy steps replayed from a CUDA graph"}
 
 
 def run_reference(args):
@@ -269,6 +276,8 @@ def main():
         solver.step(K)
         solver.dose(out=dose)
 
+    use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
+    solver.set_graphs(use_graphs)
     for _ in range(args.warmup):
         one_solve()
     torch.cuda.synchronize()
@@ -281,7 +290,9 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    solver.set_profiling(True)
+    # per-launch events of the stage kernel inside the timed region; graph replay hides
+    # individual kernels, so with graphs they come from one profiled solve afterwards
+    solver.set_profiling(not use_graphs)
     launches0 = solver.launch_count()
     times = []
     with torch.cuda.stream(stream):
@@ -298,9 +309,14 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ck = clocks.stop()
+    launches = solver.launch_count() - launches0
+    if use_graphs:
+        solver.set_profiling(True)
+        with torch.cuda.stream(stream):
+            one_solve()
+        torch.cuda.synchronize()
     stage_ms, stage_count = solver.kernel_stats()
     solver.set_profiling(False)
-    launches = solver.launch_count() - launches0
     ms_per_solve = float(np.sum(times) / args.steps)
     if ws > 1:
         t = torch.tensor([ms_per_solve], device=dev)
@@ -332,12 +348,14 @@ def main():
                 "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
                 "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
+                "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
                 "achieved_gbs": gbs, "hbm_frac": frac_hbm, "avg_launch_us": avg_launch_ms * 1000.0}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
                 "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
                 "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
                 "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "alu_frac": frac_alu,
+                "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
                 "avg_launch_us": avg_launch_ms * 1000.0}
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -402,7 +420,7 @@ def main():
                 "energy_steps_per_s": value,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": vs_plain, "adjoint": adj}
+                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs}
         if args.workload != WORKLOAD:
             line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
                               "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,

@@ -205,6 +205,15 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval);
 dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
                           double* dL_dw, int32_t out_on_device);
 
+/* enable = 1: dlra_step captures the work of its n energy steps into a CUDA graph the
+ * first time it runs from a given step with a given set of active beams, and replays the
+ * graph afterwards (ranks live on the device, so the launch sequence depends on nothing
+ * else); repeated solves after dlra_reset then cost one graph launch each. Graphs are
+ * dropped when materials, beams or the checkpoint interval change, and bypassed while
+ * profiling. A capture the driver rejects falls back to direct launches and switches the
+ * option off. enable = 0 drops every graph. */
+dlra_status dlra_set_graphs(dlra_ctx* ctx, int32_t enable);
+
 /* Per-kernel timing with CUDA events on the context's stream. enable = 1 records an
  * event pair around every launch of the fused streaming-stage kernel (the K-step
  * RK4 stage: stencil + r x r mix) until disabled; dlra_kernel_stats synchronises and

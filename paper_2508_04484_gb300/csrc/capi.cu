@@ -363,6 +363,14 @@ struct Lane {
   double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr;
 };
 
+// dlra_step(n) from a given step and beam-activity pattern, captured as a CUDA graph
+struct StepGraph {
+  int start = 0, n = 0;
+  std::vector<char> active_before, active_after;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
 }  // namespace
 
 struct dlra_ctx {
@@ -409,6 +417,10 @@ struct dlra_ctx {
   void* adj = nullptr;
   std::vector<double> tau_coef;   // per material: Sigma_t / T_w factor rho_i kappa_i g0_i
   size_t sbeta_cap = 0;
+  // CUDA-graph replay of dlra_step (dlra_set_graphs)
+  bool graphs = false;
+  cudaStream_t cap_st = nullptr;
+  std::vector<StepGraph> step_graphs;
   // streaming-stage kernel timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -843,6 +855,74 @@ dlra_status check_device_errors(dlra_ctx* ctx) {
 template <typename T>
 std::vector<Beam<T>>& beams_of(dlra_ctx* ctx) {
   return *reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams);
+}
+
+void drop_graphs(dlra_ctx* ctx) {
+  for (auto& g : ctx->step_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->step_graphs.clear();
+}
+
+template <typename T>
+std::vector<char> active_flags(dlra_ctx* ctx) {
+  std::vector<char> a;
+  for (auto& B : beams_of<T>(ctx)) a.push_back(B.active ? 1 : 0);
+  return a;
+}
+
+template <typename T>
+void set_active_flags(dlra_ctx* ctx, const std::vector<char>& a) {
+  auto& bs = beams_of<T>(ctx);
+  for (size_t b = 0; b < bs.size() && b < a.size(); ++b) bs[b].active = a[b] != 0;
+}
+
+// dlra_step through a CUDA graph: the work of n energy steps from the current step (ranks
+// live on the device, so the launch sequence depends only on the step range and on which
+// beams are active) is captured once on a private stream and replayed on the context stream.
+// A capture that fails falls back to launching the kernels directly.
+template <typename T>
+dlra_status step_graph(dlra_ctx* ctx, int n) {
+  const std::vector<char> before = active_flags<T>(ctx);
+  for (auto& g : ctx->step_graphs)
+    if (g.start == ctx->step && g.n == n && g.active_before == before) {
+      CK(cudaGraphLaunch(g.exec, ctx->st));
+      ctx->launches += g.launches;
+      ctx->step += n;
+      set_active_flags<T>(ctx, g.active_after);
+      return DLRA_OK;
+    }
+  if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+  const int step0 = ctx->step;
+  const int64_t l0 = ctx->launches;
+  cudaStream_t user = ctx->st;
+  CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeRelaxed));
+  ctx->st = ctx->cap_st;
+  dlra_status s = Engine<T>{ctx}.step_all(n);
+  ctx->st = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_st, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (s == DLRA_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (s != DLRA_OK || e != cudaSuccess || !exec) {
+    cudaGetLastError();
+    if (ctx->poisoned == DLRA_ERR_CUDA) ctx->poisoned = DLRA_OK;
+    ctx->step = step0;
+    ctx->launches = l0;
+    set_active_flags<T>(ctx, before);
+    ctx->graphs = false;
+    return Engine<T>{ctx}.step_all(n);
+  }
+  StepGraph g;
+  g.start = step0;
+  g.n = n;
+  g.active_before = before;
+  g.active_after = active_flags<T>(ctx);
+  g.exec = exec;
+  g.launches = ctx->launches - l0;
+  ctx->step_graphs.push_back(std::move(g));
+  CK(cudaGraphLaunch(exec, ctx->st));
+  return DLRA_OK;
 }
 
 template <typename T>
@@ -1699,6 +1779,8 @@ dlra_status dlra_set_materials(dlra_ctx* ctx, int32_t n_mat, const dlra_material
   if (ctx->poisoned) return ctx->poisoned;
   if (ctx->materials_set && n_mat != ctx->M)
     return fail(ctx, DLRA_ERR_STATE, "materials can be replaced only with the same number (%d)", ctx->M);
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
   if (n_mat < 1 || !mats || !w) return fail(ctx, DLRA_ERR_ARG, "need n_mat >= 1, mats and w");
   if (n_mat > ctx->RB) return fail(ctx, DLRA_ERR_ARG, "n_mat must not exceed the rank capacity");
   for (int i = 0; i < n_mat; ++i) {
@@ -1755,6 +1837,8 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval) {
   if (ctx->poisoned) return ctx->poisoned;
   if (checkpoint_interval < 0) return fail(ctx, DLRA_ERR_ARG, "checkpoint_interval must be >= 0");
   if (ctx->step != 0) return fail(ctx, DLRA_ERR_STATE, "the reverse sweep must be enabled before the first step");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
   if (checkpoint_interval != ctx->ckpt_interval) {
     if (ctx->fp64) for (auto& B : beams_of<double>(ctx)) B.ckpt.clear();
     else for (auto& B : beams_of<float>(ctx)) B.ckpt.clear();
@@ -1811,6 +1895,8 @@ dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id
   if (ctx->step > 0) return fail(ctx, DLRA_ERR_STATE, "beams must be added before the first step");
   if (!(beam->weight >= 0) || !(beam->spot_sigma >= 0) || !(beam->energy_sigma >= 0))
     return fail(ctx, DLRA_ERR_ARG, "beam weight and sigmas must be >= 0");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
   return ctx->fp64 ? add_beam_t<double>(ctx, beam, beam_id) : add_beam_t<float>(ctx, beam, beam_id);
 }
 
@@ -1826,7 +1912,20 @@ dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
     dlra_status s = ctx->fp64 ? ensure_checkpoints<double>(ctx) : ensure_checkpoints<float>(ctx);
     if (s != DLRA_OK) return s;
   }
+  if (ctx->graphs && !ctx->profiling && n_steps > 0)
+    return ctx->fp64 ? step_graph<double>(ctx, n_steps) : step_graph<float>(ctx, n_steps);
   return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
+}
+
+dlra_status dlra_set_graphs(dlra_ctx* ctx, int32_t enable) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  ctx->graphs = enable != 0;
+  if (!ctx->graphs) {
+    CK(cudaStreamSynchronize(ctx->st));
+    drop_graphs(ctx);
+  }
+  return DLRA_OK;
 }
 
 dlra_status dlra_dose(dlra_ctx* ctx, double* out, int32_t out_on_device, int32_t per_mass) {
@@ -1972,6 +2071,8 @@ void dlra_destroy(dlra_ctx* ctx) {
     if (l.s0) cudaStreamSynchronize(l.s0);
     if (l.s1) cudaStreamSynchronize(l.s1);
   }
+  drop_graphs(ctx);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto& l : ctx->lanes) {
     for (cudaEvent_t e : l.ev)

@@ -48,3 +48,27 @@ def test_concurrent_beams_match_sequential_and_oracle():
     for b in range(3):
         assert np.array_equal(logs[b], res[b]["ranks"]), b
     assert rel_l2(doses[1], ref) < 1e-5
+
+
+def test_graph_replay_matches_direct_launches():
+    from paper_2508_04484_gb300 import dlra as D
+    cfg, mats, w, beams = _case()
+    s = D.Solver(dict(cfg, max_concurrent_beams=3), mats, w, beams)
+    ref = s.run()
+    l_direct = s.launch_count()
+    s.set_graphs(True)
+    for _ in range(3):                       # capture on the first pass, replay afterwards
+        s.reset(retrace=True)
+        d = s.run()
+        assert rel_l2(d, ref) < 1e-12
+    assert s.launch_count() > 3 * l_direct // 2    # replays count the kernels they contain
+    # split solves are separate graphs; profiling bypasses them
+    s.reset(retrace=True)
+    s.step(4)
+    s.set_profiling(True)
+    s.step(3)
+    s.set_profiling(False)
+    s.step(cfg["n_steps"] - 7)
+    assert rel_l2(s.dose(), ref) < 1e-12
+    s.set_graphs(False)
+    s.close()
