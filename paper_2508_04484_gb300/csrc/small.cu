@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
   __shared__ int order[128];
   __shared__ T nrm[128];   // squared column norms, updated by each rotation
   __shared__ T red[32];
-  __shared__ int s_rot, s_r1;
+  __shared__ int cols[128];       // the columns that are not numerically null (plus -1 if odd)
+  __shared__ unsigned s_maxrel;   // largest relative coupling |a_p . a_q| / (|a_p| |a_q|) of a sweep
+  __shared__ int s_na, s_r1;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   T part = 0;
   for (int e = tid; e < n2 * n2; e += nt) {
@@ -186,25 +188,52 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
   const T eps = (sizeof(T) == 8) ? T(1e-14) : T(4e-6);
   // columns below this squared norm are numerically null and are not rotated
   const T null2 = fro2 * ((sizeof(T) == 8) ? T(1e-28) : T(1e-14));
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) s_rot = 0;
+  // after a sweep whose largest coupling c has c^2 below this, the next sweep (quadratic
+  // convergence) would rotate by less than eps: stop
+  const float stop2 = (sizeof(T) == 8) ? 1e-16f : 1e-7f;
+  if (tid == 0) {
+    int na = 0;
+    for (int j = 0; j < n2; ++j)
+      if (nrm[j] > null2) cols[na++] = j;
+    if (na & 1) cols[na++] = -1;
+    s_na = na;
+  }
+  __syncthreads();
+  const int na = s_na;
+  for (int sweep = 0; sweep < 60 && na >= 2; ++sweep) {
+    if (tid == 0) s_maxrel = 0u;
     __syncthreads();
-    for (int round = 0; round < n2 - 1; ++round) {
-      for (int pi = wid; pi < n2 / 2; pi += nw) {
-        int p, q;
-        rr_pair(round, pi, n2, p, q);
+    // round-robin over the active columns: each round rotates na/2 disjoint pairs, one per warp
+    for (int round = 0; round < na - 1; ++round) {
+      for (int pi = wid; pi < na / 2; pi += nw) {
+        int pp, qq;
+        rr_pair(round, pi, na, pp, qq);
+        const int p = cols[pp], q = cols[qq];
+        if (p < 0 || q < 0) continue;
         const T al = nrm[p], be = nrm[q];
         if (al <= null2 || be <= null2) continue;
         T* ap = A + p * n2;
         T* aq = A + q * n2;
-        T ga = 0;
-        for (int i = lane; i < n2; i += 32) ga += ap[i] * aq[i];
+        const T x0 = lane < n2 ? ap[lane] : T(0), y0 = lane < n2 ? aq[lane] : T(0);
+        const T x1 = lane + 32 < n2 ? ap[lane + 32] : T(0), y1 = lane + 32 < n2 ? aq[lane + 32] : T(0);
+        T ga = x0 * y0 + x1 * y1;
+        for (int i = lane + 64; i < n2; i += 32) ga += ap[i] * aq[i];
         ga = warp_sum(ga);
-        if (ga != T(0) && fabs(ga) > eps * sqrt(al * be)) {
+        const T rel = fabs(ga) / sqrt(al * be);
+        if (lane == 0) atomicMax(&s_maxrel, __float_as_uint((float)rel));
+        if (ga != T(0) && rel > eps) {
           T zeta = (be - al) / (T(2) * ga);
           T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           T c = T(1) / sqrt(T(1) + t * t), s = c * t;
-          for (int i = lane; i < n2; i += 32) {
+          if (lane < n2) {
+            ap[lane] = c * x0 - s * y0;
+            aq[lane] = s * x0 + c * y0;
+          }
+          if (lane + 32 < n2) {
+            ap[lane + 32] = c * x1 - s * y1;
+            aq[lane + 32] = s * x1 + c * y1;
+          }
+          for (int i = lane + 64; i < n2; i += 32) {
             T x = ap[i], y = aq[i];
             ap[i] = c * x - s * y;
             aq[i] = s * x + c * y;
@@ -216,12 +245,10 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
             vp[i] = c * x - s * y;
             vq[i] = s * x + c * y;
           }
-          __syncwarp();
           if (lane == 0) {
             // exact norms of the rotated pair: |a_p|^2 - t ga, |a_q|^2 + t ga
             nrm[p] = al - t * ga;
             nrm[q] = be + t * ga;
-            s_rot = 1;
           }
         }
       }
@@ -235,7 +262,8 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
       if (lane == 0) nrm[j] = s2;
     }
     __syncthreads();
-    if (!s_rot) break;
+    const float mr = __uint_as_float(s_maxrel);
+    if (mr <= (float)eps || mr * mr < stop2) break;
     __syncthreads();
   }
   for (int j = wid; j < n2; j += nw) {
