@@ -205,6 +205,13 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval);
 dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
                           double* dL_dw, int32_t out_on_device);
 
+/* enable = 1: on the FP32-mixed path, the streaming stage runs on the fifth-generation tensor
+ * cores (tcgen05.mma kind::tf32 with the operands split into high and low TF32 parts, FP32
+ * accuracy; accumulators in tensor memory) instead of FP32 FMA. Measured slower than the FMA
+ * kernel on the 64^3, rank-20 workload (the stage is bound by its stencil loads, not by the
+ * r x r products), so it is off by default. No effect on the FP64 path. */
+dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable);
+
 /* enable = 1: dlra_step captures the work of its n energy steps into a CUDA graph the
  * first time it runs from a given step with a given set of active beams, and replays the
  * graph afterwards (ranks live on the device, so the launch sequence depends on nothing

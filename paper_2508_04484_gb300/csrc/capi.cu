@@ -31,6 +31,7 @@
 #include "../../include/dlra.h"
 #include "device.cuh"
 #include "kernels.h"
+#include "kstage_tc.cuh"
 #include "tables.h"
 
 using namespace dlra;
@@ -204,7 +205,17 @@ constexpr int kRankCaps[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
 
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
-                   const Geo& g, const T* Pst, const int* rdim, T beta, int last) {
+                   const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, bool tensor_cores) {
+  if constexpr (sizeof(T) == 4) {
+    if (tensor_cores) {
+      // FP32 path on request: the r x r mix on the tensor cores (3xTF32)
+      const size_t smem = kstage_tc_smem<NACT, RM>();
+      cudaFuncSetAttribute(kstage_tc_kernel<NACT, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kstage_tc_kernel<NACT, RM><<<kstage_tc_grid<NACT, RM>(g), 256, smem, st>>>(vin, y, yout, vout, n, inv_rho, g,
+                                                                                 Pst, rdim, beta, last, err);
+      return;
+    }
+  }
   size_t smem = (size_t)2 * NACT * RM * RM * sizeof(T);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kstage_kernel<T, RM, NACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -214,10 +225,11 @@ void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, 
 
 template <typename T, int NACT>
 void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n,
-                     const T* inv_rho, const Geo& g, const T* Pst, const int* rdim, T beta, int last) {
+                     const T* inv_rho, const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err,
+                     bool tc) {
   switch (RB) {
 #define KS_CASE(R) \
-  case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last); break;
+  case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc); break;
     KS_CASE(4) KS_CASE(8) KS_CASE(12) KS_CASE(16) KS_CASE(20) KS_CASE(24) KS_CASE(32)
     KS_CASE(40) KS_CASE(48) KS_CASE(64)
 #undef KS_CASE
@@ -228,9 +240,10 @@ void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout,
 // one RK4 Horner stage of the K-step on the scaled input vin = rho^-1 z
 template <typename T>
 void kstage(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
-            const Geo& g, const T* Pst, const int* rdim, T beta, int last, int64_t& nl) {
-  if (g.nact == 3) kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last);
-  else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last);
+            const Geo& g, const T* Pst, const int* rdim, T beta, int last, int64_t& nl, int* err = nullptr,
+            bool tc = false) {
+  if (g.nact == 3) kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
+  else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
   ++nl;
 }
 
@@ -417,6 +430,8 @@ struct dlra_ctx {
   void* adj = nullptr;
   std::vector<double> tau_coef;   // per material: Sigma_t / T_w factor rho_i kappa_i g0_i
   size_t sbeta_cap = 0;
+  // tcgen05 K-stage kernel on the FP32 path (dlra_set_tensor_cores)
+  bool tensor_cores = false;
   // CUDA-graph replay of dlra_step (dlra_set_graphs)
   bool graphs = false;
   cudaStream_t cap_st = nullptr;
@@ -706,14 +721,14 @@ struct Engine {
           const int sf = 3 - s2;
           const T* vin = s2 == 0 ? va : capq(4 * j + sf + 1);
           kstage<T>(RB, st, vin, y, y, capq(4 * j + sf), n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[sf]), 2, nl);
+                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tensor_cores);
         } else if (cap) {
           T* vout = s2 < 3 ? capq(4 * j + s2 + 1) : (j + 1 < ns ? capq(4 * (j + 1)) : vb);
           kstage<T>(RB, st, capq(4 * j + s2), y, y, vout, n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tensor_cores);
         } else {
           kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tensor_cores);
         }
         prof_end(ctx, st);
         double lbeta[4];
@@ -849,6 +864,7 @@ dlra_status check_device_errors(dlra_ctx* ctx) {
   if (h & ERR_NONFINITE) return fail(ctx, DLRA_ERR_NONFINITE, "the low-rank state became non-finite");
   if (h & ERR_CHOLESKY) return fail(ctx, DLRA_ERR_NONFINITE, "implicit scattering matrix is not positive definite");
   if (h & ERR_CAPACITY) return fail(ctx, DLRA_ERR_RANK, "rank capacity rank_max exceeded");
+  if (h & ERR_TIMEOUT) return fail(ctx, DLRA_ERR_TIMEOUT, "a bounded device-side wait gave up");
   return DLRA_OK;
 }
 
@@ -1915,6 +1931,15 @@ dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
   if (ctx->graphs && !ctx->profiling && n_steps > 0)
     return ctx->fp64 ? step_graph<double>(ctx, n_steps) : step_graph<float>(ctx, n_steps);
   return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
+}
+
+dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->tensor_cores = enable != 0;
+  return DLRA_OK;
 }
 
 dlra_status dlra_set_graphs(dlra_ctx* ctx, int32_t enable) {

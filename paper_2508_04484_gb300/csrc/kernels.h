@@ -13,7 +13,7 @@ struct BeamDims {
   int pad;
 };
 
-enum ErrBits { ERR_NONFINITE = 1, ERR_CHOLESKY = 2, ERR_CAPACITY = 4 };
+enum ErrBits { ERR_NONFINITE = 1, ERR_CHOLESKY = 2, ERR_CAPACITY = 4, ERR_TIMEOUT = 8 };
 
 struct RankParams {
   int mode;          // 0 fixed, 1 adaptive, 2 schedule

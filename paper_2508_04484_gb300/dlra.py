@@ -84,6 +84,7 @@ SIGNATURES = {
     "dlra_set_beam_weight": ([_P, C.c_int32, C.c_double], C.c_int),
     "dlra_enable_adjoint": ([_P, C.c_int32], C.c_int),
     "dlra_backward": ([_P, _P, C.c_int32, _DP, _P, C.c_int32], C.c_int),
+    "dlra_set_tensor_cores": ([_P, C.c_int32], C.c_int),
     "dlra_set_graphs": ([_P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
@@ -318,6 +319,10 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
     return dbeta[:n_beams], dw
 
 
+def dlra_set_tensor_cores(ctx, enable=True):
+    _check(ctx, load().dlra_set_tensor_cores(ctx, int(bool(enable))))
+
+
 def dlra_set_graphs(ctx, enable=True):
     _check(ctx, load().dlra_set_graphs(ctx, int(bool(enable))))
 
@@ -455,6 +460,10 @@ class Solver:
 
     def set_profiling(self, enable=True):
         dlra_set_profiling(self.ctx, enable)
+
+    def set_tensor_cores(self, enable=True):
+        """Run the streaming stage on the tcgen05 tensor cores (FP32-mixed path)."""
+        dlra_set_tensor_cores(self.ctx, enable)
 
     def set_graphs(self, enable=True):
         """Capture each dlra_step call as a CUDA graph and replay it on repeated solves."""

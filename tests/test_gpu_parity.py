@@ -144,6 +144,28 @@ def test_heterogeneous_cube_fp32_matches_oracle():
     s.close()
 
 
+@pytest.mark.parametrize("case", ["slab", "cube"])
+def test_tensor_core_stage_matches_oracle(case):
+    # the tcgen05 (3xTF32) streaming stage against the FMA stage and the oracle
+    if case == "slab":
+        cfg, mats, w, beams = _slab(precision=WL.FP32_MIXED)
+        mode, kw = OP.FIXED, dict(rank=6)
+    else:
+        cfg, mats, w, beams = _cube()
+        mode, kw = OP.ADAPTIVE, dict(tol=1e-3, r_max=12)
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    dose, res = oracle_dlra(prob, src, mode, **kw)
+    doses = []
+    for tc in (False, True):
+        s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=WL.FP32_MIXED)
+        s.set_tensor_cores(tc)
+        doses.append(s.run())
+        s.close()
+    assert rel_l2(doses[1], doses[0]) < 1e-5
+    assert rel_l2(doses[1], dose) < 1e-3
+
+
 def test_state_errors():
     from paper_2508_04484_gb300 import dlra as D
     cfg, mats, w, beams = _slab()
