@@ -1,6 +1,7 @@
 // Small dense kernels of the low-rank step (one thread block each): the factors
 // of the basis augmentation, the truncation SVD, the Galerkin S-step, the implicit
 // collided L-step and its QR, the W-side augmentation and the source S assembly.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -475,9 +476,120 @@ __global__ void __launch_bounds__(1024) sstep_kernel(const double* __restrict__ 
   }
 }
 
+// The S-step on a cluster of SCL thread blocks: block c owns the output columns J_c of
+// S -> sum_k G_k S P_k (Sec. 2.2, Eq. KLS). Per RK4 stage it forms U_k = z P_k(:, J_c) and
+// sum_k G_k U_k for its columns, and writes its part of the next stage input z into the
+// shared memory of every block of the cluster (distributed shared memory); one cluster
+// barrier per stage. z is double-buffered so that a stage never overwrites the buffer the
+// other blocks are still reading.
+constexpr int SCL = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) sstep_cluster_kernel(const double* __restrict__ Gh,
+                                                            const double* __restrict__ Ph, int nk,
+                                                            const double* __restrict__ S, int RB, int n2,
+                                                            const double* __restrict__ beta, int nsub,
+                                                            double* __restrict__ Sh) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int w = (n2 + SCL - 1) / SCL;                 // columns per block
+  const int j0 = rank * w, jn = max(0, min(w, n2 - j0));
+  const int ne = n2 * n2;
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* G = reinterpret_cast<T*>(raw);                   // nk x n2 x n2, G_k[a][q] at (k n2 + q) n2 + a
+  T* Pc = G + (size_t)nk * ne;                        // nk x n2 x w: P_k[q][j0 + j] at (k w + j) n2 + q
+  T* z0 = Pc + (size_t)nk * n2 * w;                   // two stage buffers, n2 x n2 column-major
+  T* z1 = z0 + ne;
+  T* U = z1 + ne;                                     // nk x n2 x w
+  double* y = reinterpret_cast<double*>(U + (size_t)nk * n2 * w);   // own columns of Sh, n2 x w
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < nk * ne; e += nt) G[e] = T(Gh[e]);
+  for (int e = tid; e < nk * n2 * w; e += nt) {
+    const int q = e % n2, kj = e / n2, j = kj % w, k = kj / w;
+    Pc[e] = (j < jn) ? T(Ph[((long long)k * n2 + j0 + j) * n2 + q]) : T(0);
+  }
+  for (int e = tid; e < ne; e += nt) {
+    const int a = e % n2, c = e / n2;
+    z0[e] = T((a < RB && c < RB) ? S[c * RB + a] : 0.0);
+  }
+  for (int e = tid; e < n2 * w; e += nt) {
+    const int a = e % n2, j = e / n2, c = j0 + j;
+    y[e] = (j < jn && a < RB && c < RB) ? S[c * RB + a] : 0.0;
+  }
+  __syncthreads();
+  int stage = 0;
+  for (int js = 0; js < nsub; ++js) {
+    for (int s4 = 0; s4 < 4; ++s4, ++stage) {
+      const double b = beta[4 * js + s4];
+      const T* z = (stage & 1) ? z1 : z0;
+      T* zn = (stage & 1) ? z0 : z1;
+      // U_k(:, j) = z P_k(:, j0 + j)
+      for (int e = tid; e < nk * n2 * w; e += nt) {
+        const int a = e % n2, kj = e / n2;
+        const T* pc = Pc + (size_t)kj * n2;
+        T acc = T(0);
+        for (int q = 0; q < n2; ++q) acc += z[q * n2 + a] * pc[q];
+        U[e] = acc;
+      }
+      __syncthreads();
+      // out(:, j) = sum_k G_k U_k(:, j); y / z update of the own columns
+      for (int e = tid; e < n2 * jn; e += nt) {
+        const int a = e % n2, j = e / n2;
+        T acc = T(0);
+        for (int k = 0; k < nk; ++k) {
+          const T* gk = G + (size_t)k * ne + a;
+          const T* uk = U + ((size_t)k * w + j) * n2;
+          for (int q = 0; q < n2; ++q) acc += gk[q * n2] * uk[q];
+        }
+        const double nv = y[e] + b * (double)acc;
+        if (s4 == 3) y[e] = nv;
+        const T tv = T(nv);
+        const int col = j0 + j;
+        for (int rk = 0; rk < SCL; ++rk) {
+          T* dst = cluster.map_shared_rank(zn, rk);
+          dst[col * n2 + a] = tv;
+        }
+      }
+      cluster.sync();
+    }
+  }
+  for (int e = tid; e < n2 * jn; e += nt) {
+    const int a = e % n2, j = e / n2;
+    Sh[(long long)(j0 + j) * n2 + a] = y[e];
+  }
+}
+
+template <typename T>
+size_t sstep_cluster_smem(int nk, int n2) {
+  const int w = (n2 + SCL - 1) / SCL;
+  return ((size_t)nk * n2 * n2 + 2 * (size_t)nk * n2 * w + 2 * (size_t)n2 * n2) * sizeof(T) +
+         (size_t)n2 * w * sizeof(double) + 16;
+}
+
 template <typename T>
 void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
                   const double* beta, int nsub, double* Sh) {
+  const size_t csmem = sstep_cluster_smem<T>(nk, n2);
+  if (csmem <= 200 * 1024) {
+    if (csmem > 48 * 1024)
+      cudaFuncSetAttribute(sstep_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(SCL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = csmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, sstep_cluster_kernel<T>, Gh, Ph, nk, S, RB, n2, beta, nsub, Sh) == cudaSuccess)
+      return;
+    cudaGetLastError();   // cluster launch refused: fall back to one block
+  }
   const size_t ne = (size_t)n2 * n2;
   const size_t full = (2 + 2 * (size_t)nk) * ne * sizeof(T);
   const int preload = full <= 200 * 1024 ? 1 : 0;
