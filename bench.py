@@ -44,6 +44,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
                    help="replay the energy steps from CUDA graphs (auto: on for multi-beam workloads)")
     p.add_argument("--energy-steps", type=int, default=0,
@@ -276,6 +277,7 @@ def main():
         solver.step(K)
         solver.dose(out=dose)
 
+    tuned = solver.autotune() if not args.no_autotune else None
     use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
     solver.set_graphs(use_graphs)
     for _ in range(args.warmup):
@@ -420,7 +422,7 @@ def main():
                 "energy_steps_per_s": value,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs}
+                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs, "autotune": tuned}
         if args.workload != WORKLOAD:
             line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
                               "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,

@@ -205,6 +205,15 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval);
 dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
                           double* dL_dw, int32_t out_on_device);
 
+/* Autotuner: times the launch variants of the heavy cell-side kernels on this context's work
+ * space (filled with synthetic values at full rank capacity) and keeps the fastest: the FMA or
+ * tensor-core streaming stage (FP32 path), the grid of the Gram reductions (608 / 1216 / 2432 /
+ * 4864 target blocks) and of the stencil Grams (0.5 / 1 / 2 waves). Needs materials and a beam;
+ * synchronises; drops captured graphs. report (optional, 12 doubles): the measured ms of each
+ * variant in that order (-1 where not applicable), then the chosen stage variant (1 = tensor
+ * cores), Gram block target and stencil-Gram waves x 2. */
+dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
+
 /* enable = 1: on the FP32-mixed path, the streaming stage runs on the fifth-generation tensor
  * cores (tcgen05.mma kind::tf32 with the operands split into high and low TF32 parts, FP32
  * accuracy; accumulators in tensor memory) instead of FP32 FMA. Measured slower than the FMA

@@ -166,6 +166,34 @@ __global__ void set_int_kernel(int* p, int v) { *p = v; }
 // ---------------------------------------------------------------------------
 // launch helpers for the tiled product and the Gram reduction
 // ---------------------------------------------------------------------------
+// Launch geometry chosen by dlra_autotune for the context being stepped on this thread.
+struct Tuning {
+  int gram_blocks = 1216;     // target number of blocks of the Gram reductions (x the 2-D tile grid)
+  int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x 152 blocks
+  int kstage_tc = 0;          // 1: tcgen05 streaming stage on the FP32 path
+};
+thread_local const Tuning* t_tuning = nullptr;
+const Tuning& tuning() {
+  static const Tuning def;
+  return t_tuning ? *t_tuning : def;
+}
+struct TuneScope {
+  const Tuning* prev;
+  explicit TuneScope(const Tuning* t) : prev(t_tuning) { t_tuning = t; }
+  ~TuneScope() { t_tuning = prev; }
+};
+
+template <typename T>
+__global__ void fill_pseudo_random_kernel(T* p, long long cnt, unsigned seed, T scale) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  unsigned h = (unsigned)i * 2654435761u ^ seed;
+  h ^= h >> 15;
+  h *= 2246822519u;
+  h ^= h >> 13;
+  p[i] = scale * (T((h & 0xFFFFFF) * (1.0 / 16777216.0)) - T(0.5));
+}
+
 template <typename T, int BK, class AL, class BL, class EP>
 void gemm(cudaStream_t st, long long rows, int N, int Q, AL al, BL bl, EP ep, int64_t& nl) {
   if (rows <= 0 || N <= 0) return;
@@ -187,13 +215,13 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
   int gy = (acap + tile - 1) / tile, gz = (ncols_j + tile - 1) / tile;
   long long want = (rows + GR_TC - 1) / GR_TC;
   if (tile == 64) {
-    long long cap = std::max(1, 1216 / (gy * gz));
+    long long cap = std::max(1, tuning().gram_blocks / (gy * gz));
     int gx = (int)std::max(1LL, std::min(want, cap));
     gram_kernel<T, F, 64, 1><<<dim3(gx, gy, gz), 256, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
   } else {
     // row groups per block: 4 (FP32) / 2 (FP64) keep the static staging below 48 KB
     constexpr int RG = sizeof(T) == 4 ? 4 : 2;
-    long long cap = std::max(1, 1216 / (gy * gz));
+    long long cap = std::max(1, tuning().gram_blocks / (gy * gz));
     int gx = (int)std::max(1LL, std::min((want + RG - 1) / RG, cap));
     gram_kernel<T, F, 32, RG><<<dim3(gx, gy, gz), 64 * RG, 0, st>>>(rows, A, lda, adim, acap, ncols_j, f, out, ldo);
   }
@@ -269,7 +297,8 @@ void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, in
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   per_sm = std::max(per_sm, 1);
-  const int gx = (int)std::max(1LL, std::min(chunks, (long long)std::max(1, 152 * per_sm / nslice)));
+  const int gx = (int)std::max(
+      1LL, std::min(chunks, (long long)std::max(1, 152 * per_sm * tuning().gs_waves_x2 / 2 / nslice)));
   kern<<<dim3(gx, nslice), threads, smem, st>>>(rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, jslice, out,
                                                 ldj, ldo);
   ++nl;
@@ -430,8 +459,9 @@ struct dlra_ctx {
   void* adj = nullptr;
   std::vector<double> tau_coef;   // per material: Sigma_t / T_w factor rho_i kappa_i g0_i
   size_t sbeta_cap = 0;
-  // tcgen05 K-stage kernel on the FP32 path (dlra_set_tensor_cores)
-  bool tensor_cores = false;
+  // launch geometry and kernel variants (dlra_autotune, dlra_set_tensor_cores)
+  Tuning tun;
+  BeamDims* tune_dims = nullptr;
   // CUDA-graph replay of dlra_step (dlra_set_graphs)
   bool graphs = false;
   cudaStream_t cap_st = nullptr;
@@ -721,14 +751,14 @@ struct Engine {
           const int sf = 3 - s2;
           const T* vin = s2 == 0 ? va : capq(4 * j + sf + 1);
           kstage<T>(RB, st, vin, y, y, capq(4 * j + sf), n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tensor_cores);
+                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
         } else if (cap) {
           T* vout = s2 < 3 ? capq(4 * j + s2 + 1) : (j + 1 < ns ? capq(4 * (j + 1)) : vb);
           kstage<T>(RB, st, capq(4 * j + s2), y, y, vout, n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tensor_cores);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
         } else {
           kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tensor_cores);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
         }
         prof_end(ctx, st);
         double lbeta[4];
@@ -1574,6 +1604,99 @@ dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int ou
   return DLRA_OK;
 }
 
+// Times the launch variants of the heavy n-side kernels on lane 0's work space filled with
+// synthetic values (rank = capacity) and keeps the fastest. report (optional, 12 doubles): ms of
+// the FMA / tensor-core streaming stage, of the Gram reduction at 608 / 1216 / 2432 / 4864
+// target blocks, of the stencil Gram at 0.5 / 1 / 2 waves, then the chosen stage variant,
+// Gram block target and stencil-Gram waves x 2.
+template <typename T>
+dlra_status autotune_t(dlra_ctx* ctx, double* report) {
+  Engine<T> E{ctx};
+  E.L = &ctx->lanes[0];
+  Lane& L = *E.L;
+  cudaStream_t st = L.s0;
+  const long long n = ctx->n;
+  const int RB = ctx->RB, n2 = ctx->n2, nk = ctx->nk;
+  int64_t nl = 0;
+  CK(cudaStreamSynchronize(ctx->st));
+  if (!ctx->tune_dims) {
+    ALLOC(ctx->tune_dims, sizeof(BeamDims));
+  }
+  BeamDims dh{RB, RB, RB, 0};
+  CK(cudaMemcpy(ctx->tune_dims, &dh, sizeof dh, cudaMemcpyHostToDevice));
+  const int* rdim = &ctx->tune_dims->r;
+  for (int i = 0; i < 3; ++i)
+    fill_pseudo_random_kernel<T><<<nblk(n * RB, 256), 256, 0, st>>>(E.P(L.Kb[i]), n * RB, 17u + i, T(1));
+  fill_pseudo_random_kernel<T><<<nblk(n * n2, 256), 256, 0, st>>>(E.P(L.Xh), n * n2, 29u, T(1));
+  fill_pseudo_random_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(E.P(L.Pst), (long long)nk * RB * RB,
+                                                                                  31u, T(0.1));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_ms = [&](auto&& launch) {
+    for (int w = 0; w < 2; ++w) launch();
+    cudaEventRecord(e0, st);
+    for (int w = 0; w < 5; ++w) launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return (double)ms / 5.0;
+  };
+  Tuning t = ctx->tun;
+  TuneScope scope(&t);
+  double rep[12] = {0};
+  // streaming stage: FMA or tensor cores (FP32 path)
+  for (int v = 0; v < 2; ++v) {
+    if (v == 1 && sizeof(T) != 4) {
+      rep[1] = -1.0;
+      continue;
+    }
+    rep[v] = time_ms([&] {
+      kstage<T>(RB, st, E.P(L.Kb[1]), E.P(L.Kb[0]), E.P(L.Kb[0]), E.P(L.Kb[2]), n, E.P(ctx->inv_rho), ctx->geo,
+                E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v == 1);
+    });
+  }
+  // Gram reduction X^_{:, RB:}^T X^ (the second augmentation pass's shape)
+  const int gb[4] = {608, 1216, 2432, 4864};
+  for (int v = 0; v < 4; ++v) {
+    t.gram_blocks = gb[v];
+    rep[2 + v] = time_ms([&] {
+      gram<T>(st, n, E.P(L.Xh), n, nullptr, n2, RB, FPlain<T>{E.P(L.Xh) + (long long)RB * n, n, nullptr, RB}, L.Cg,
+              n2, nl);
+    });
+  }
+  // stencil Gram on the augmented basis
+  const int gw[3] = {1, 2, 4};
+  for (int v = 0; v < 3; ++v) {
+    t.gs_waves_x2 = gw[v];
+    rep[6 + v] = time_ms([&] {
+      gram_stencil<T>(st, n, E.P(L.Xh), n, n2, nullptr, E.P(L.Xh), n, n2, nullptr, E.P(ctx->inv_rho), ctx->geo, L.Gc,
+                      n2, n2, nl);
+    });
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  Tuning best = ctx->tun;
+  best.kstage_tc = (rep[1] > 0.0 && rep[1] < rep[0]) ? 1 : 0;
+  int bi = 0;
+  for (int v = 1; v < 4; ++v)
+    if (rep[2 + v] < rep[2 + bi]) bi = v;
+  best.gram_blocks = gb[bi];
+  int wi = 0;
+  for (int v = 1; v < 3; ++v)
+    if (rep[6 + v] < rep[6 + wi]) wi = v;
+  best.gs_waves_x2 = gw[wi];
+  rep[9] = best.kstage_tc;
+  rep[10] = best.gram_blocks;
+  rep[11] = best.gs_waves_x2;
+  ctx->tun = best;
+  if (report) std::memcpy(report, rep, sizeof rep);
+  return DLRA_OK;
+}
+
 template <typename T>
 void free_beams(dlra_ctx* ctx) {
   delete reinterpret_cast<std::vector<Beam<T>>*>(ctx->beams);
@@ -1897,6 +2020,7 @@ dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_devi
   double* ge = ctx->fp64 ? reinterpret_cast<AdjWork<double>*>(ctx->adj)->ge
                          : reinterpret_cast<AdjWork<float>*>(ctx->adj)->ge;
   CK(cudaMemcpyAsync(ge, gh.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  TuneScope scope(&ctx->tun);
   s = ctx->fp64 ? backward_t<double>(ctx, dL_dweight, dL_dw, out_on_device)
                 : backward_t<float>(ctx, dL_dweight, dL_dw, out_on_device);
   if (s != DLRA_OK) return s;
@@ -1928,9 +2052,19 @@ dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
     dlra_status s = ctx->fp64 ? ensure_checkpoints<double>(ctx) : ensure_checkpoints<float>(ctx);
     if (s != DLRA_OK) return s;
   }
+  TuneScope scope(&ctx->tun);
   if (ctx->graphs && !ctx->profiling && n_steps > 0)
     return ctx->fp64 ? step_graph<double>(ctx, n_steps) : step_graph<float>(ctx, n_steps);
   return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
+}
+
+dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (!ctx->materials_set || ctx->lanes.empty()) return fail(ctx, DLRA_ERR_STATE, "autotuning needs materials and a beam");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  return ctx->fp64 ? autotune_t<double>(ctx, report) : autotune_t<float>(ctx, report);
 }
 
 dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
@@ -1938,7 +2072,7 @@ dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
   if (ctx->poisoned) return ctx->poisoned;
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
-  ctx->tensor_cores = enable != 0;
+  ctx->tun.kstage_tc = enable != 0 ? 1 : 0;
   return DLRA_OK;
 }
 

@@ -72,3 +72,18 @@ def test_graph_replay_matches_direct_launches():
     assert rel_l2(s.dose(), ref) < 1e-12
     s.set_graphs(False)
     s.close()
+
+
+def test_autotuned_launches_give_the_same_dose():
+    from paper_2508_04484_gb300 import dlra as D
+    cfg, mats, w, beams = _case()
+    cfg = dict(cfg, precision=WL.FP32_MIXED)
+    s = D.Solver(cfg, mats, w, beams)
+    ref = s.run()
+    rep = s.autotune()
+    assert rep["stage_fma_ms"] > 0 and rep["stage_tensor_core_ms"] > 0
+    assert rep["gram_blocks"] in (608, 1216, 2432, 4864)
+    s.reset(retrace=True)
+    d = s.run()
+    assert rel_l2(d, ref) < 1e-5
+    s.close()
