@@ -26,6 +26,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dlra.h"
@@ -209,6 +210,22 @@ template <typename T, class F>
 void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int* adim, int acap, int ncols_j, F f,
           double* out, long long ldo, int64_t& nl) {
   if (rows <= 0 || acap <= 0 || ncols_j <= 0) return;
+  if constexpr (std::is_same<F, FPlain<T>>::value) {
+    if (ncols_j <= 2 && rows >= 4096) {
+      // a few columns (the source step's rank-M updates): a bandwidth-bound reduction
+      // at least eight rows per thread: the block reduction at the end costs ~5 x 32 shuffles
+      const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((rows + 2047) / 2048, 152 * 2));
+      const dim3 grid(gx, (unsigned)((acap + 31) / 32));
+      if (ncols_j == 1)
+        gram_narrow_kernel<T, 1><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j,
+                                                       out, ldo);
+      else
+        gram_narrow_kernel<T, 2><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j,
+                                                       out, ldo);
+      ++nl;
+      return;
+    }
+  }
   const long long area64 = (long long)((acap + 63) / 64) * ((ncols_j + 63) / 64) * 4096;
   const long long area32 = (long long)((acap + 31) / 32) * ((ncols_j + 31) / 32) * 1024;
   const int tile = area32 < area64 ? 32 : 64;

@@ -769,6 +769,59 @@ struct FStencil {  // F(row, k * nb + b) = D_k(rho^-1 B[:, b])(row), tables per 
 
 
 
+// Narrow Gram: out[j * ldo + a] += sum_i A(i, a) B(i, j) for at most NJ columns of B. One
+// thread per row (coalesced column reads), 32 columns of A per block row (blockIdx.y), the
+// partial sums reduced over the block and added with FP64 atomics. Memory-bound: A is read once.
+template <typename T, int NJ>
+__global__ void __launch_bounds__(256) gram_narrow_kernel(long long rows, const T* __restrict__ A, long long lda,
+                                                          const int* adim, int acap, const T* __restrict__ B,
+                                                          long long ldb, const int* bdim, int bcap, int ncols_j,
+                                                          double* __restrict__ out, long long ldo) {
+  __shared__ double red[8][32 * NJ];
+  const int a0 = blockIdx.y * 32;
+  const int Aact = min(dev_dim(adim, acap), acap);
+  const int Bact = min(dev_dim(bdim, bcap), ncols_j);
+  const int na = min(32, Aact - a0);
+  T acc[32][NJ];
+#pragma unroll
+  for (int a = 0; a < 32; ++a)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[a][j] = T(0);
+  if (na > 0) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+         i += (long long)gridDim.x * blockDim.x) {
+      T f[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) f[j] = j < Bact ? B[(long long)j * ldb + i] : T(0);
+#pragma unroll
+      for (int a = 0; a < 32; ++a) {
+        if (a < na) {
+          const T v = A[(long long)(a0 + a) * lda + i];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) acc[a][j] += v * f[j];
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < 32; ++a)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      double v = (double)acc[a][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][a * NJ + j] = v;
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * NJ; e += blockDim.x) {
+    const int a = e / NJ, j = e - a * NJ;
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][e];
+    if (a < na && j < ncols_j && v != 0.0) atomicAdd(out + (long long)j * ldo + a0 + a, v);
+  }
+}
+
 template <typename T, class F, int TILE, int RG>
 __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __restrict__ A, long long lda,
                                                    const int* adim, int acap, int ncols_j, F f,
