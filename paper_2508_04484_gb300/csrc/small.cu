@@ -44,7 +44,9 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
                                    double drop_tol, double* __restrict__ Mout, int* qout, int* err) {
   extern __shared__ double sh[];
   __shared__ double red[32];
+  __shared__ double rdiag[128];          // 1 / L_ii
   __shared__ int s_piv, s_stop;
+  __shared__ int iperm[128];             // original column -> pivoted position
   const int ldg = RBa + qcap;
   double* A = sh;                        // qcap x qcap, col-major A[j*qcap + i]
   double* Li = A + qcap * qcap;          // inverse of the lower factor
@@ -67,16 +69,29 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
   if (tid == 0) s_stop = qcap;
   __syncthreads();
   for (int j = 0; j < qcap; ++j) {
-    if (tid == 0) {
-      int p = j;
-      double best = A[j * qcap + j];
-      for (int i = j + 1; i < qcap; ++i)
-        if (A[i * qcap + i] > best) { best = A[i * qcap + i]; p = i; }
-      if (!(best > thr)) {
-        s_stop = j;
-        if (best != best) atomicOr(err, ERR_NONFINITE);
+    if (tid < 32) {
+      // largest remaining diagonal (first index on ties), one warp
+      int p = -1;
+      double best = 0.0;
+      bool nan = false;
+      for (int i = j + tid; i < qcap; i += 32) {
+        const double d = A[i * qcap + i];
+        nan = nan || d != d;
+        if (p < 0 || d > best) { best = d; p = i; }
       }
-      s_piv = p;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (op >= 0 && (p < 0 || ob > best || (ob == best && op < p))) { best = ob; p = op; }
+      }
+      nan = __any_sync(0xffffffffu, nan);
+      if (tid == 0) {
+        if (!(best > thr) || nan) {
+          s_stop = j;
+          if (nan || best != best) atomicOr(err, ERR_NONFINITE);
+        }
+        s_piv = p;
+      }
     }
     __syncthreads();
     if (s_stop == j) break;
@@ -112,12 +127,15 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
     __syncthreads();
   }
   const int q = s_stop;
+  for (int i = tid; i < q; i += nt) rdiag[i] = 1.0 / A[i * qcap + i];
+  for (int i = tid; i < qcap; i += nt) iperm[perm[i]] = i;
+  __syncthreads();
   // inverse of the lower factor L (q x q): column c solves L x = e_c
   for (int c = tid; c < q; c += nt) {
     for (int i = 0; i < q; ++i) {
       double v = (i == c) ? 1.0 : 0.0;
       for (int k = c; k < i; ++k) v -= A[k * qcap + i] * Li[c * qcap + k];
-      Li[c * qcap + i] = (i < c) ? 0.0 : v / A[i * qcap + i];
+      Li[c * qcap + i] = (i < c) ? 0.0 : v * rdiag[i];
     }
   }
   __syncthreads();
@@ -128,9 +146,8 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
     double v = 0.0;
     if (c < q) {
       if (row >= RBa) {
-        int jj = row - RBa;  // original index
-        for (int i = 0; i < q; ++i)
-          if (perm[i] == jj) { v = Li[i * qcap + c]; break; }
+        const int i = iperm[row - RBa];   // pivoted position of the original column
+        v = i < q ? Li[i * qcap + c] : 0.0;
       } else {
         for (int i = 0; i < q; ++i) v -= G[(long long)perm[i] * ldg + row] * Li[i * qcap + c];
       }
