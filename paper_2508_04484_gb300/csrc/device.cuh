@@ -846,6 +846,49 @@ __global__ void __launch_bounds__(256) gram_kernel(long long rows, const T* __re
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   const long long stride = (long long)gridDim.x * RG * GR_TC;
   const long long nchunk_iter = (rows + stride - 1) / stride;
+  if constexpr (!F::kTables) {
+    // software pipeline: the next chunk's values are loaded into registers while the
+    // current chunk is multiplied out of shared memory
+    constexpr int PER = GR_TC * TILE / GT;   // staged values per thread and operand
+    T ra[PER], rf[PER];
+    auto load = [&](long long it) {
+      const long long r0 = it * stride + ((long long)blockIdx.x * RG + g) * GR_TC;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * GT;
+        const int t = e % GR_TC, c = e / GR_TC;
+        const long long r = r0 + t;
+        const int a = a0 + c, j = j0 + c;
+        ra[u] = (r < rows && a < Aact && a < acap) ? A[(long long)a * lda + r] : T(0);
+        rf[u] = (r < rows && j < ncols_j) ? f(r, j, Jact, t, nullptr, nullptr) : T(0);
+      }
+    };
+    if (nchunk_iter > 0) load(0);
+    for (long long it = 0; it < nchunk_iter; ++it) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * GT;
+        const int t = e % GR_TC, c = e / GR_TC;
+        sA[g][t][c] = ra[u];
+        sF[g][t][c] = rf[u];
+      }
+      __syncthreads();
+      if (it + 1 < nchunk_iter) load(it + 1);
+#pragma unroll 8
+      for (int t = 0; t < GR_TC; ++t) {
+        T a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = sA[g][t][ta + TPD * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = sF[g][t][tj + TPD * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      }
+      __syncthreads();
+    }
+  } else
   for (long long it = 0; it < nchunk_iter; ++it) {
     const long long r0 = it * stride + ((long long)blockIdx.x * RG + g) * GR_TC;
     if (F::kTables) {
