@@ -206,13 +206,21 @@ dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_devi
                           double* dL_dw, int32_t out_on_device);
 
 /* Autotuner: times the launch variants of the heavy cell-side kernels on this context's work
- * space (filled with synthetic values at full rank capacity) and keeps the fastest: the FMA or
- * tensor-core streaming stage (FP32 path), the grid of the Gram reductions (608 / 1216 / 2432 /
- * 4864 target blocks) and of the stencil Grams (0.5 / 1 / 2 waves). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 12 doubles): the measured ms of each
- * variant in that order (-1 where not applicable), then the chosen stage variant (1 = tensor
- * cores), Gram block target and stencil-Gram waves x 2. */
+ * space (filled with synthetic values at full rank capacity) and keeps the fastest: the
+ * streaming stage per cell with FMA, on the tensor cores (FP32 path) or per brick with FMA and
+ * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
+ * blocks) and of the stencil Grams (0.5 / 1 / 2 waves). Needs materials and a beam;
+ * synchronises; drops captured graphs. report (optional, 13 doubles): ms of the per-cell and
+ * tensor-core stages, of the four Gram grids, of the three stencil-Gram grids, the chosen stage
+ * variant (0 per cell, 1 tensor cores, 2 brick), Gram block target, stencil-Gram waves x 2, and
+ * ms of the brick stage (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
+
+/* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
+ * 1 the tensor-core kernel of dlra_set_tensor_cores (FP32 path; the FMA kernel on FP64),
+ * 2 one block per 256-cell brick with the stencil inputs staged in shared memory. Same results
+ * up to rounding; dlra_autotune picks among them. */
+dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* enable = 1: on the FP32-mixed path, the streaming stage runs on the fifth-generation tensor
  * cores (tcgen05.mma kind::tf32 with the operands split into high and low TF32 parts, FP32

@@ -171,7 +171,7 @@ __global__ void set_int_kernel(int* p, int v) { *p = v; }
 struct Tuning {
   int gram_blocks = 1216;     // target number of blocks of the Gram reductions (x the 2-D tile grid)
   int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x 152 blocks
-  int kstage_tc = 0;          // 1: tcgen05 streaming stage on the FP32 path
+  int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA
 };
 thread_local const Tuning* t_tuning = nullptr;
 const Tuning& tuning() {
@@ -250,9 +250,20 @@ constexpr int kRankCaps[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
 
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
-                   const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, bool tensor_cores) {
+                   const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant) {
+  if (variant == 2) {
+    using Bk = Brick<NACT>;
+    const size_t smem = ((size_t)2 * NACT * RM * RM + 2 * Bk::HALO) * sizeof(T);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kstage_brick_kernel<T, RM, NACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned grid = (unsigned)(((g.nx + Bk::TX - 1) / Bk::TX) * ((g.ny + Bk::TY - 1) / Bk::TY) *
+                                     ((g.nz + Bk::TZ - 1) / Bk::TZ));
+    kstage_brick_kernel<T, RM, NACT><<<grid, 256, smem, st>>>(vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta,
+                                                               last);
+    return;
+  }
   if constexpr (sizeof(T) == 4) {
-    if (tensor_cores) {
+    if (variant == 1) {
       // FP32 path on request: the r x r mix on the tensor cores (3xTF32)
       const size_t smem = kstage_tc_smem<NACT, RM>();
       cudaFuncSetAttribute(kstage_tc_kernel<NACT, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -271,7 +282,7 @@ void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, 
 template <typename T, int NACT>
 void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n,
                      const T* inv_rho, const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err,
-                     bool tc) {
+                     int tc) {
   switch (RB) {
 #define KS_CASE(R) \
   case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc); break;
@@ -286,7 +297,7 @@ void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout,
 template <typename T>
 void kstage(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
             const Geo& g, const T* Pst, const int* rdim, T beta, int last, int64_t& nl, int* err = nullptr,
-            bool tc = false) {
+            int tc = 0) {
   if (g.nact == 3) kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
   else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
   ++nl;
@@ -768,14 +779,14 @@ struct Engine {
           const int sf = 3 - s2;
           const T* vin = s2 == 0 ? va : capq(4 * j + sf + 1);
           kstage<T>(RB, st, vin, y, y, capq(4 * j + sf), n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
+                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tun.kstage_variant);
         } else if (cap) {
           T* vout = s2 < 3 ? capq(4 * j + s2 + 1) : (j + 1 < ns ? capq(4 * (j + 1)) : vb);
           kstage<T>(RB, st, capq(4 * j + s2), y, y, vout, n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant);
         } else {
           kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_tc != 0);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant);
         }
         prof_end(ctx, st);
         double lbeta[4];
@@ -1662,18 +1673,21 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[12] = {0};
-  // streaming stage: FMA or tensor cores (FP32 path)
-  for (int v = 0; v < 2; ++v) {
+  double rep[13] = {0};
+  // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA
+  double stage_ms[3];
+  for (int v = 0; v < 3; ++v) {
     if (v == 1 && sizeof(T) != 4) {
-      rep[1] = -1.0;
+      stage_ms[v] = -1.0;
       continue;
     }
-    rep[v] = time_ms([&] {
+    stage_ms[v] = time_ms([&] {
       kstage<T>(RB, st, E.P(L.Kb[1]), E.P(L.Kb[0]), E.P(L.Kb[0]), E.P(L.Kb[2]), n, E.P(ctx->inv_rho), ctx->geo,
-                E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v == 1);
+                E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v);
     });
   }
+  rep[0] = stage_ms[0];
+  rep[1] = stage_ms[1];
   // Gram reduction X^_{:, RB:}^T X^ (the second augmentation pass's shape)
   const int gb[4] = {608, 1216, 2432, 4864};
   for (int v = 0; v < 4; ++v) {
@@ -1697,7 +1711,10 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   Tuning best = ctx->tun;
-  best.kstage_tc = (rep[1] > 0.0 && rep[1] < rep[0]) ? 1 : 0;
+  int sv = 0;
+  for (int v = 1; v < 3; ++v)
+    if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
+  best.kstage_variant = sv;
   int bi = 0;
   for (int v = 1; v < 4; ++v)
     if (rep[2 + v] < rep[2 + bi]) bi = v;
@@ -1706,7 +1723,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   for (int v = 1; v < 3; ++v)
     if (rep[6 + v] < rep[6 + wi]) wi = v;
   best.gs_waves_x2 = gw[wi];
-  rep[9] = best.kstage_tc;
+  rep[9] = best.kstage_variant;
+  rep[12] = stage_ms[2];
   rep[10] = best.gram_blocks;
   rep[11] = best.gs_waves_x2;
   ctx->tun = best;
@@ -2084,12 +2102,22 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
   return ctx->fp64 ? autotune_t<double>(ctx, report) : autotune_t<float>(ctx, report);
 }
 
+dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (variant < 0 || variant > 2) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0, 1 or 2");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->tun.kstage_variant = variant;
+  return DLRA_OK;
+}
+
 dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
-  ctx->tun.kstage_tc = enable != 0 ? 1 : 0;
+  ctx->tun.kstage_variant = enable != 0 ? 1 : 0;
   return DLRA_OK;
 }
 

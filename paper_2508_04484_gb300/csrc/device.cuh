@@ -477,6 +477,129 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
   }
 }
 
+// Cell bricks of the staged streaming stage: 256 cells per block (8 x 8 x 4 in 3-D,
+// 16 x 1 x 16 in a 2-D slab) and their two-cell halo.
+template <int NACT>
+struct Brick {
+  static constexpr int TX = NACT == 3 ? 8 : 16, TY = NACT == 3 ? 8 : 1, TZ = NACT == 3 ? 4 : 16;
+  static constexpr int HX = TX + 4, HY = NACT == 3 ? TY + 4 : 1, HZ = TZ + 4;
+  static constexpr int HALO = HX * HY * HZ;
+  static constexpr int HPT = (HALO + 255) / 256;   // halo values staged per thread
+};
+
+// The streaming stage of kstage_kernel with the stencil inputs staged per brick: for each
+// input column the block loads the brick and its halo into shared memory once (coalesced
+// x-rows; the next column's values are in flight during the current column's products), and
+// every thread forms its cell's six (four) stencil values from there instead of loading 13
+// neighbours from global memory. Same modes and outputs as kstage_kernel.
+template <typename T, int RM, int NACT>
+__global__ void __launch_bounds__(256, (RM * sizeof(T) <= 96) ? 4 : 2) kstage_brick_kernel(const T* __restrict__ vin, const T* __restrict__ y,
+                                                           T* __restrict__ yout, T* __restrict__ vout, long long ld,
+                                                           const T* __restrict__ inv_rho, Geo g,
+                                                           const T* __restrict__ Pst, const int* __restrict__ rdim,
+                                                           T beta, int last) {
+  using Bk = Brick<NACT>;
+  constexpr int NK = 2 * NACT;
+  constexpr int TX = Bk::TX, TY = Bk::TY, HX = Bk::HX, HY = Bk::HY, HALO = Bk::HALO, HPT = Bk::HPT;
+  constexpr int SYH = HX, SZH = HX * HY;
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* sP = reinterpret_cast<T*>(raw);
+  T* sH = sP + NK * RM * RM;   // two halo buffers
+  const int tid = threadIdx.x;
+  const int r = dev_dim(rdim, RM);
+  for (int e = tid; e < NK * RM * r; e += blockDim.x) sP[e] = Pst[e];
+  const int bx = (g.nx + TX - 1) / TX, by = (g.ny + TY - 1) / TY;
+  const int blk = blockIdx.x;
+  const int x0 = (blk % bx) * TX, y0 = ((blk / bx) % by) * TY, z0 = (blk / (bx * by)) * Bk::TZ;
+  const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+  const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+  const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+  const long long i = ((long long)iz * g.ny + iy) * g.nx + ix;
+  const int hc = (lz + 2) * SZH + (NACT == 3 ? (ly + 2) * SYH : 0) + (lx + 2);
+  int hcell[HPT];
+#pragma unroll
+  for (int u = 0; u < HPT; ++u) {
+    const int h = tid + 256 * u;
+    hcell[u] = -2;
+    if (h < HALO) {
+      const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+      const int gx = x0 + hx - 2, gy = NACT == 3 ? y0 + hy - 2 : y0, gz = z0 + hz - 2;
+      hcell[u] = (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz)
+                     ? (int)(((long long)gz * g.ny + gy) * g.nx + gx)
+                     : -1;
+    }
+  }
+  T inv2[NACT];
+#pragma unroll
+  for (int da = 0; da < NACT; ++da) inv2[da] = T(g.inv2d[(NACT == 3) ? da : (da == 0 ? 0 : 2)]);
+  T acc[RM];
+#pragma unroll
+  for (int c = 0; c < RM; ++c) acc[c] = T(0);
+  T pre[HPT];
+  auto fetch = [&](int c) {
+    const T* col = vin + (long long)c * ld;
+#pragma unroll
+    for (int u = 0; u < HPT; ++u) pre[u] = hcell[u] >= 0 ? col[hcell[u]] : T(0);
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < HPT; ++u)
+      if (hcell[u] != -2) sH[buf * HALO + tid + 256 * u] = pre[u];
+  };
+  if (r > 0) {
+    fetch(0);
+    stash(0);
+  }
+  __syncthreads();
+  for (int c = 0; c < r; ++c) {
+    if (c + 1 < r) fetch(c + 1);
+    const T* hv = sH + (c & 1) * HALO + hc;
+    const T v0 = hv[0];
+    T sv[NK];
+#pragma unroll
+    for (int da = 0; da < NACT; ++da) {
+      const int st = NACT == 3 ? (da == 0 ? 1 : (da == 1 ? SYH : SZH)) : (da == 0 ? 1 : SZH);
+      sv[2 * da] = (T(-3) * v0 + T(4) * hv[-st] - hv[-2 * st]) * inv2[da];
+      sv[2 * da + 1] = (T(3) * v0 - T(4) * hv[st] + hv[2 * st]) * inv2[da];
+    }
+    const T* Pc = sP + (long long)c * NK * RM;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+#pragma unroll
+      for (int cp = 0; cp < RM; cp += 4) {
+        T p4[4];
+        Vec4<T>::load(Pc + k * RM + cp, p4);
+        acc[cp] += sv[k] * p4[0];
+        acc[cp + 1] += sv[k] * p4[1];
+        acc[cp + 2] += sv[k] * p4[2];
+        acc[cp + 3] += sv[k] * p4[3];
+      }
+    }
+    if (c + 1 < r) stash((c + 1) & 1);
+    __syncthreads();
+  }
+  if (!ok) return;
+  const T ir0 = inv_rho[i];
+  if (last == 2) {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      const T lam = beta * ir0 * acc[c];
+      vout[(long long)c * ld + i] = lam;
+      yout[(long long)c * ld + i] = y[(long long)c * ld + i] + lam;
+    }
+  } else if (last) {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      const T yn = y[(long long)c * ld + i] + beta * acc[c];
+      yout[(long long)c * ld + i] = yn;
+      vout[(long long)c * ld + i] = ir0 * yn;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RM; ++c) vout[(long long)c * ld + i] = ir0 * (y[(long long)c * ld + i] + beta * acc[c]);
+  }
+}
+
 template <typename T>
 struct EpiStoreScaled {  // C = acc and V = rho^-1 acc
   T* C;

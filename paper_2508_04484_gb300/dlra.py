@@ -85,6 +85,7 @@ SIGNATURES = {
     "dlra_enable_adjoint": ([_P, C.c_int32], C.c_int),
     "dlra_backward": ([_P, _P, C.c_int32, _DP, _P, C.c_int32], C.c_int),
     "dlra_autotune": ([_P, _DP], C.c_int),
+    "dlra_set_stage_kernel": ([_P, C.c_int32], C.c_int),
     "dlra_set_tensor_cores": ([_P, C.c_int32], C.c_int),
     "dlra_set_graphs": ([_P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
@@ -322,11 +323,17 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(12)
+    rep = np.zeros(13)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
-    return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
-                stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), tensor_core_stage=bool(rep[9]),
+    return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
+                gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
+                stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])),
+                stage_variant=("per-cell FMA", "tensor cores", "brick FMA")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0)
+
+
+def dlra_set_stage_kernel(ctx, variant: int):
+    _check(ctx, load().dlra_set_stage_kernel(ctx, int(variant)))
 
 
 def dlra_set_tensor_cores(ctx, enable=True):
@@ -474,6 +481,10 @@ class Solver:
     def autotune(self):
         """Time the launch variants of the heavy kernels here and keep the fastest."""
         return dlra_autotune(self.ctx)
+
+    def set_stage_kernel(self, variant):
+        """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA."""
+        dlra_set_stage_kernel(self.ctx, variant)
 
     def set_tensor_cores(self, enable=True):
         """Run the streaming stage on the tcgen05 tensor cores (FP32-mixed path)."""

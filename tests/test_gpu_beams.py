@@ -81,7 +81,7 @@ def test_autotuned_launches_give_the_same_dose():
     s = D.Solver(cfg, mats, w, beams)
     ref = s.run()
     rep = s.autotune()
-    assert rep["stage_fma_ms"] > 0 and rep["stage_tensor_core_ms"] > 0
+    assert rep["stage_fma_ms"] > 0 and rep["stage_tensor_core_ms"] > 0 and rep["stage_brick_ms"] > 0
     assert rep["gram_blocks"] in (608, 1216, 2432, 4864)
     s.reset(retrace=True)
     d = s.run()

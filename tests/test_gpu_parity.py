@@ -144,9 +144,11 @@ def test_heterogeneous_cube_fp32_matches_oracle():
     s.close()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("case", ["slab", "cube"])
-def test_tensor_core_stage_matches_oracle(case):
-    # the tcgen05 (3xTF32) streaming stage against the FMA stage and the oracle
+def test_stage_kernel_variants_match_oracle(case, variant):
+    # the tcgen05 (3xTF32) and the brick-staged streaming stages against the per-cell stage
+    # and the oracle
     if case == "slab":
         cfg, mats, w, beams = _slab(precision=WL.FP32_MIXED)
         mode, kw = OP.FIXED, dict(rank=6)
@@ -157,13 +159,24 @@ def test_tensor_core_stage_matches_oracle(case):
     src = oracle_sources(prob, beams)
     dose, res = oracle_dlra(prob, src, mode, **kw)
     doses = []
-    for tc in (False, True):
+    for v in (0, variant):
         s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=WL.FP32_MIXED)
-        s.set_tensor_cores(tc)
+        s.set_stage_kernel(v)
         doses.append(s.run())
         s.close()
     assert rel_l2(doses[1], doses[0]) < 1e-5
     assert rel_l2(doses[1], dose) < 1e-3
+
+
+def test_brick_stage_fp64_matches_oracle():
+    cfg, mats, w, beams = _slab(precision=WL.FP64)
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    dose, res = oracle_dlra(prob, src, OP.FIXED, rank=6)
+    s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=WL.FP64)
+    s.set_stage_kernel(2)
+    assert rel_l2(s.run(), dose) < 1e-5
+    s.close()
 
 
 def test_state_errors():
