@@ -200,10 +200,19 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval);
  * The adjoint state is a low-rank factorisation advanced by the same BUG steps with
  * the transposed operators (its rank control: the forward's, adaptive when the forward
  * replays a schedule); forward states are recomputed from the checkpoints of
- * dlra_enable_adjoint, one segment at a time. Requires dlra_enable_adjoint before the
- * first step (else DLRA_ERR_STATE). Synchronises. The forward state is unchanged. */
+ * dlra_enable_adjoint, one segment at a time (see dlra_set_adjoint_store). Requires
+ * dlra_enable_adjoint before the first step (else DLRA_ERR_STATE). Synchronises. The
+ * forward state is unchanged. */
 dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_device, double* dL_dweight,
                           double* dL_dw, int32_t out_on_device);
+
+/* Memory/time trade of dlra_backward's segment replay. keep = 1 (default): while replaying a
+ * segment of I energy steps, keep each step's streaming-stage inputs (4 n_sub buffers of
+ * n x capacity) and post-collision state, so the reverse steps reuse them; taken only when
+ * they fit in a third of the free device memory, else as keep = 0. keep = 0: store only the
+ * start state of each step and recompute the forward step during the reverse sweep. Same
+ * results either way up to the summation order of the FP64 atomic reductions. */
+dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
 
 /* Autotuner: times the launch variants of the heavy cell-side kernels on this context's work
  * space (filled with synthetic values at full rank capacity) and keeps the fastest: the

@@ -411,6 +411,13 @@ struct AdjWork {
   T* capf = nullptr;          // forward K-stage inputs rho^-1 z of one energy step
   T* capa = nullptr;          // their adjoints
   int cap_ns = 0;
+  // with room on the device, the replay keeps every step's K-stage inputs and post-collision
+  // state of the segment, so that the reverse steps need not recompute them
+  bool store = false;
+  T* capseg = nullptr;        // [step of segment][beam] x 4 nsub_max stage buffers
+  size_t capseg_stride = 0;   // elements per (step, beam)
+  size_t capseg_slots = 0;
+  std::vector<Snap<T>> segb;  // post-collision states [step of segment][beam]
   T* gvec = nullptr;          // dL/de in the n-side type
   double *ge = nullptr, *be0 = nullptr, *gtmp = nullptr;
   double *grad_rho = nullptr, *grad_f = nullptr, *grad_tau = nullptr, *grad_w = nullptr, *dw = nullptr;
@@ -484,6 +491,7 @@ struct dlra_ctx {
   std::vector<int> ray_count;
   // reverse sweep: checkpoint interval (0 = off) and its work space (AdjWork<T>*)
   int ckpt_interval = 0;
+  int adj_store = 1;  // reverse sweep keeps the replayed segment's stage inputs when they fit
   void* adj = nullptr;
   std::vector<double> tau_coef;   // per material: Sigma_t / T_w factor rho_i kappa_i g0_i
   size_t sbeta_cap = 0;
@@ -524,6 +532,18 @@ dlra_status fail(dlra_ctx* c, dlra_status s, const char* fmt, ...) {
       return fail(ctx, e_ == cudaErrorMemoryAllocation ? DLRA_ERR_OOM : DLRA_ERR_CUDA,      \
                   "%s failed: %s", #call, cudaGetErrorString(e_));                            \
   } while (0)
+
+// frees one allocation made by dalloc (device-synchronising)
+void dfree(dlra_ctx* ctx, void* p) {
+  if (!p) return;
+  for (auto& a : ctx->allocs)
+    if (a == p) {
+      cudaFree(p);
+      a = ctx->allocs.back();
+      ctx->allocs.pop_back();
+      return;
+    }
+}
 
 dlra_status dalloc(dlra_ctx* ctx, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -1116,6 +1136,35 @@ dlra_status alloc_adj(dlra_ctx* ctx) {
     ALLOC(A.capa, sizeof(T) * (size_t)4 * ctx->nsub_max * n * RB);
     A.cap_ns = ctx->nsub_max;
   }
+  {
+    // keep the forward stage inputs of a whole segment when they fit in a third of the free memory
+    const size_t stride = (size_t)4 * ctx->nsub_max * n * RB;
+    const size_t need = stride * sizeof(T) * ctx->ckpt_interval * nb +
+                        (size_t)ctx->ckpt_interval * nb * (sizeof(T) * ((size_t)n + m) * RB + sizeof(double) * RB * RB);
+    const size_t slots = (size_t)ctx->ckpt_interval * nb;
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    if (!ctx->adj_store) {
+      A.store = false;
+    } else if (A.capseg && A.capseg_stride == stride && A.capseg_slots >= slots && A.segb.size() >= slots) {
+      A.store = true;
+    } else if (need < freeb / 3) {
+      CK(cudaStreamSynchronize(ctx->st));
+      dfree(ctx, A.capseg);
+      A.capseg = nullptr;
+      ALLOC(A.capseg, stride * sizeof(T) * slots);
+      A.capseg_stride = stride;
+      A.capseg_slots = slots;
+      while (A.segb.size() < slots) {
+        A.segb.emplace_back();
+        dlra_status s = alloc_snap<T>(ctx, A.segb.back());
+        if (s != DLRA_OK) return s;
+      }
+      A.store = true;
+    } else {
+      A.store = false;
+    }
+  }
   while (A.seg.size() < (size_t)ctx->ckpt_interval * nb) {
     A.seg.emplace_back();
     dlra_status s = alloc_snap<T>(ctx, A.seg.back());
@@ -1559,12 +1608,16 @@ dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int ou
       Beam<T>& B = bs[b];
       E.snap_load(B.ckpt[sg], A.rep, st);
       for (int k = k0; k < k1; ++k) {
-        E.snap_save(A.rep, A.seg[(size_t)(k - k0) * nb + b], st);
-        if (k + 1 == k1) break;
+        const size_t slot = (size_t)(k - k0) * nb + b;
+        E.snap_save(A.rep, A.seg[slot], st);
+        const bool last = k + 1 == k1;
+        if (last && !A.store) break;
         if (active_at(b, k)) {
-          E.streaming(A.rep, k);
+          E.streaming(A.rep, k, 0, A.store ? A.capseg + slot * A.capseg_stride : nullptr);
           E.scattering(A.rep, k);
+          if (A.store) E.snap_save(A.rep, A.segb[slot], st);
         }
+        if (last) break;
         if (B.has_src[k]) E.source_with(A.rep, k, nullptr, B.Bsrc + (long long)k * M * m, M, B.psi + (long long)k * n);
       }
     }
@@ -1596,15 +1649,36 @@ dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int ou
       for (int b = 0; b < nb; ++b) {
         if (!active_at(b, k)) continue;
         Beam<T>& B = bs[b];
-        E.snap_load(A.seg[(size_t)(k - k0) * nb + b], A.rep, st);
+        const size_t slot = (size_t)(k - k0) * nb + b;
+        // forward quantities of step k: the start state's W (K-step basis), the K-stage inputs
+        // and the post-collision state; kept by the replay, or recomputed from the start state
+        const T* Wf;
+        const T* cf;
+        const T* Xb;
+        const T* Wb;
+        const double* Sb;
+        if (A.store) {
+          Wf = A.seg[slot].W;
+          cf = A.capseg + slot * A.capseg_stride;
+          Xb = A.segb[slot].X;
+          Wb = A.segb[slot].W;
+          Sb = A.segb[slot].S;
+        } else {
+          E.snap_load(A.seg[slot], A.rep, st);
+          Wf = A.seg[slot].W;
+          E.streaming(A.rep, k, 0, A.capf);
+          E.scattering(A.rep, k);
+          cf = A.capf;
+          Xb = A.rep.X;
+          Wb = A.rep.W;
+          Sb = A.rep.S;
+        }
         // C = W_f^T W_alpha: the forward K-step basis against the adjoint K-step basis
         cudaMemsetAsync(A.Cm, 0, sizeof(double) * RB * RB, st);
-        gram<T>(st, m, A.rep.W, m, nullptr, RB, RB, FPlain<T>{A.alpha.W, m, nullptr, RB}, A.Cm, RB, nl);
-        E.streaming(A.rep, k, 0, A.capf);
-        E.scattering(A.rep, k);
-        launch_grad_stream<T>(st, A.capf, A.capa, 4 * ns, n, RB, A.Cm, B.weight, A.grad_rho);
-        launch_scatter_cl(st, A.alpha.S, A.alpha.W, A.rep.S, A.rep.W, sizeof(T) == 8 ? 1 : 0, m, N, RB, A.Cl);
-        launch_grad_scatter<T>(st, A.alpha.X, A.rep.X, n, RB, A.Cl, N, ctx->coef + (long long)k * M * (N + 1), M,
+        gram<T>(st, m, Wf, m, nullptr, RB, RB, FPlain<T>{A.alpha.W, m, nullptr, RB}, A.Cm, RB, nl);
+        launch_grad_stream<T>(st, cf, A.capa, 4 * ns, n, RB, A.Cm, B.weight, A.grad_rho);
+        launch_scatter_cl(st, A.alpha.S, A.alpha.W, Sb, Wb, sizeof(T) == 8 ? 1 : 0, m, N, RB, A.Cl);
+        launch_grad_scatter<T>(st, A.alpha.X, Xb, n, RB, A.Cl, N, ctx->coef + (long long)k * M * (N + 1), M,
                                E.P(ctx->wc), ctx->f_cell, B.weight, A.grad_w, A.grad_rho);
         nl += 3;
       }
@@ -2118,6 +2192,13 @@ dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = enable != 0 ? 1 : 0;
+  return DLRA_OK;
+}
+
+dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  ctx->adj_store = keep != 0;
   return DLRA_OK;
 }
 

@@ -88,6 +88,7 @@ SIGNATURES = {
     "dlra_set_stage_kernel": ([_P, C.c_int32], C.c_int),
     "dlra_set_tensor_cores": ([_P, C.c_int32], C.c_int),
     "dlra_set_graphs": ([_P, C.c_int32], C.c_int),
+    "dlra_set_adjoint_store": ([_P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
@@ -344,6 +345,10 @@ def dlra_set_graphs(ctx, enable=True):
     _check(ctx, load().dlra_set_graphs(ctx, int(bool(enable))))
 
 
+def dlra_set_adjoint_store(ctx, keep=True):
+    _check(ctx, load().dlra_set_adjoint_store(ctx, int(bool(keep))))
+
+
 def dlra_set_profiling(ctx, enable=True):
     _check(ctx, load().dlra_set_profiling(ctx, int(bool(enable))))
 
@@ -430,6 +435,10 @@ class Solver:
 
     def enable_adjoint(self, checkpoint_interval=16):
         dlra_enable_adjoint(self.ctx, checkpoint_interval)
+
+    def set_adjoint_store(self, keep=True):
+        """Keep the replayed forward stage inputs for the reverse sweep (more memory, less work)."""
+        dlra_set_adjoint_store(self.ctx, keep)
 
     def backward(self, dL_de, dw_out=None):
         """(dL/dweight per beam, dL/dw per material and cell) of a loss of the dose."""

@@ -43,9 +43,10 @@ def _case(nx=6, nz=6, N=3, K=1, collision=WL.BOLTZMANN, rank_mode=WL.FIXED, rank
     return cfg, [WATER, BONE], w, g
 
 
-def _gpu_grad(cfg, mats, w, beams, g, interval=16):
+def _gpu_grad(cfg, mats, w, beams, g, interval=16, keep=True):
     from paper_2508_04484_gb300 import dlra as D
     s = D.Solver(cfg, mats, w, beams)
+    s.set_adjoint_store(keep)
     s.enable_adjoint(interval)
     e = s.run()
     dbeta, dw = s.backward(g)
@@ -139,6 +140,18 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert rel_l2(e, out[0][0]) < 1e-12
         assert rel_l2(dbeta, out[0][1]) < 1e-12
         assert rel_l2(dw, out[0][2]) < 1e-9
+
+
+def test_kept_and_recomputed_forward_steps_agree():
+    """The reverse sweep with the replayed stage inputs kept, and with them recomputed."""
+    cfg, mats, w, g = _multi_case()
+    beams = [WL.pencil_beam(60.0, (1.1, 0.0, 0.0), (0.2, 0.0, 1.0), spot_sigma=0.1, weight=1.0),
+             WL.pencil_beam(57.0, (0.9, 0.0, 0.0), (-0.1, 0.0, 1.0), spot_sigma=0.1, weight=0.5)]
+    for interval in (3, 16):
+        kept = _gpu_grad(cfg, mats, w, beams, g, interval=interval, keep=True)
+        redo = _gpu_grad(cfg, mats, w, beams, g, interval=interval, keep=False)
+        assert rel_l2(kept[1], redo[1]) < 1e-12
+        assert rel_l2(kept[2], redo[2]) < 1e-9
 
 
 def test_beam_weights_and_mixture_replacement():
