@@ -218,11 +218,12 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * space (filled with synthetic values at full rank capacity) and keeps the fastest: the
  * streaming stage per cell with FMA, on the tensor cores (FP32 path) or per brick with FMA and
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
- * blocks) and of the stencil Grams (0.5 / 1 / 2 waves). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 13 doubles): ms of the per-cell and
- * tensor-core stages, of the four Gram grids, of the three stencil-Gram grids, the chosen stage
- * variant (0 per cell, 1 tensor cores, 2 brick), Gram block target, stencil-Gram waves x 2, and
- * ms of the brick stage (-1 where not applicable). */
+ * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
+ * kernel). Needs materials and a beam; synchronises; drops captured graphs. report (optional,
+ * 15 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 per cell, 1 tensor cores, 2 brick), Gram block
+ * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram
+ * (-1 where not applicable) and the chosen stencil-Gram kernel (0 FMA, 1 tensor cores). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -230,6 +231,13 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * 2 one block per 256-cell brick with the stencil inputs staged in shared memory. Same results
  * up to rounding; dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
+
+/* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):
+ * 0 FMA (default), 1 on the tensor cores (FP32-mixed path only: tcgen05.mma kind::tf32 with
+ * high/low TF32 splits of both operands, FP32 accumulation in tensor memory, FP64 sums across
+ * blocks; the FMA kernel on FP64 or for more than 128 columns). Same results up to rounding;
+ * dlra_autotune picks between them. */
+dlra_status dlra_set_stencil_gram_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* enable = 1: on the FP32-mixed path, the streaming stage runs on the fifth-generation tensor
  * cores (tcgen05.mma kind::tf32 with the operands split into high and low TF32 parts, FP32
@@ -300,6 +308,36 @@ dlra_status dlra_kstep(const dlra_kstep_args* args);
  * race on it. Enqueued on cuda_stream without synchronising; calls no cudaMalloc
  * or cudaFree. */
 dlra_status dlra_kstep_noalloc(const dlra_kstep_args* args);
+
+/* Arguments of the stand-alone stencil Gram (no context needed). Device memory of the current
+ * device, ordered with cuda_stream:
+ *   A  : FP32, n x na column-major with leading dimension lda >= n, n = nx ny nz;
+ *   B  : FP32, n x nb column-major with leading dimension ldb >= n;
+ *   inv_rho : FP32, n values 1/rho_s(x);
+ *   out: FP64, nk nb na values, G_k[a][b] at out[(k nb + b) na + a]; overwritten.
+ * nk and k = 2 da + s as for dlra_kstep_args.P; 1 <= na, nb <= 128. variant: 0 FMA kernel,
+ * 1 tensor-core kernel (as dlra_set_stencil_gram_kernel). */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  int32_t na, nb;
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  const float* inv_rho;
+  double* out;
+  int32_t variant;
+  void* cuda_stream;
+} dlra_stencil_gram_args;
+
+/* The Galerkin blocks of the streaming operator between two cell bases (Sec. 3.3.2, the
+ * X^T D X terms of the L-step and S-step with the one-sided second-order stencils of Eq.
+ * (D+-) and two ghost layers of zeros): G_k[a][b] = sum_i A(i, a) D_k(rho_s^-1 B(:, b))(i),
+ * summed in FP32 within a block and in FP64 across blocks. Allocates a 4-byte error flag;
+ * synchronises cuda_stream. DLRA_ERR_TIMEOUT if a tensor-core wait ran out (out is then
+ * incomplete); errors read with dlra_last_error(NULL). */
+dlra_status dlra_stencil_gram(const dlra_stencil_gram_args* args);
 
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);

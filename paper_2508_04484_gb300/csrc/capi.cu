@@ -172,6 +172,8 @@ struct Tuning {
   int gram_blocks = 1216;     // target number of blocks of the Gram reductions (x the 2-D tile grid)
   int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x 152 blocks
   int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA
+  int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path)
+  int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
 };
 thread_local const Tuning* t_tuning = nullptr;
 const Tuning& tuning() {
@@ -307,7 +309,15 @@ void kstage(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout,
 template <typename T>
 void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, int na, const int* adim, const T* B,
                   long long ldb, int nb, const int* bdim, const T* inv_rho, const Geo& g, double* out, int ldj,
-                  long long ldo, int64_t& nl) {
+                  long long ldo, int64_t& nl, int* err = nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tuning().gs_variant == 1 && gram_stencil_tc_supported(na, rows)) {
+      launch_gram_stencil_tc(st, rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, out, ldj, ldo,
+                             tuning().gs_tc_waves_x2, err);
+      ++nl;
+      return;
+    }
+  }
   const int nk = 2 * g.nact;
   const int nj = nk * nb;
   const int naP = (na + 3) / 4 * 4;
@@ -761,7 +771,8 @@ struct Engine {
                 EpiStore<T>{ly, m, nullptr, m, T(1), T(0)}, nl);
     // [n] G_k = X^T D_k rho^-1 X; K0 = X S (and rho^-1 K0)
     cudaMemsetAsync(L->G1, 0, sizeof(double) * nk * RB * RB, st);
-    gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, L->G1, RB, RB, nl);
+    gram_stencil<T>(st, n, B.X, n, RB, rdim, B.X, n, RB, rdim, P(ctx->inv_rho), ctx->geo, L->G1, RB, RB, nl,
+                    ctx->dev_err);
     gt_kernel<T><<<nblk((long long)nk * RB * RB, 256), 256, 0, st>>>(L->G1, RB, nk, P(L->GtT), adj);
     ++nl;
     cudaEventRecord(L->ev[2], st);
@@ -824,7 +835,8 @@ struct Engine {
     T* Xh = P(L->Xh);
     T* Wh = P(L->Wh);
     cudaMemsetAsync(L->Gc, 0, sizeof(double) * nk * n2 * n2, st);
-    gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, L->Gc, n2, n2, nl);
+    gram_stencil<T>(st, n, Xh, n, n2, nullptr, Xh, n, n2, nullptr, P(ctx->inv_rho), ctx->geo, L->Gc, n2, n2, nl,
+                    ctx->dev_err);
     if (adj) {
       launch_transpose_blocks(st, L->Gc, n2, nk);
       ++nl;
@@ -1707,10 +1719,11 @@ dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int ou
 }
 
 // Times the launch variants of the heavy n-side kernels on lane 0's work space filled with
-// synthetic values (rank = capacity) and keeps the fastest. report (optional, 12 doubles): ms of
+// synthetic values (rank = capacity) and keeps the fastest. report (optional, 15 doubles): ms of
 // the FMA / tensor-core streaming stage, of the Gram reduction at 608 / 1216 / 2432 / 4864
 // target blocks, of the stencil Gram at 0.5 / 1 / 2 waves, then the chosen stage variant,
-// Gram block target and stencil-Gram waves x 2.
+// Gram block target and stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core
+// stencil Gram and the chosen stencil-Gram kernel.
 template <typename T>
 dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   Engine<T> E{ctx};
@@ -1747,7 +1760,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[13] = {0};
+  double rep[15] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA
   double stage_ms[3];
   for (int v = 0; v < 3; ++v) {
@@ -1780,6 +1793,16 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
                       n2, n2, nl);
     });
   }
+  // the same stencil Gram on the tensor cores (FP32 path)
+  double gs_tc_ms = -1.0;
+  if (sizeof(T) == 4 && gram_stencil_tc_supported(n2, n)) {
+    t.gs_variant = 1;
+    gs_tc_ms = time_ms([&] {
+      gram_stencil<T>(st, n, E.P(L.Xh), n, n2, nullptr, E.P(L.Xh), n, n2, nullptr, E.P(ctx->inv_rho), ctx->geo, L.Gc,
+                      n2, n2, nl, ctx->dev_err);
+    });
+    t.gs_variant = 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
@@ -1797,6 +1820,9 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   for (int v = 1; v < 3; ++v)
     if (rep[6 + v] < rep[6 + wi]) wi = v;
   best.gs_waves_x2 = gw[wi];
+  best.gs_variant = (gs_tc_ms > 0.0 && gs_tc_ms < rep[6 + wi]) ? 1 : 0;
+  rep[13] = gs_tc_ms;
+  rep[14] = best.gs_variant;
   rep[9] = best.kstage_variant;
   rep[12] = stage_ms[2];
   rep[10] = best.gram_blocks;
@@ -2195,6 +2221,16 @@ dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
   return DLRA_OK;
 }
 
+dlra_status dlra_set_stencil_gram_kernel(dlra_ctx* ctx, int32_t variant) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (variant < 0 || variant > 1) return fail(ctx, DLRA_ERR_ARG, "stencil Gram variant must be 0 or 1");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->tun.gs_variant = variant;
+  return DLRA_OK;
+}
+
 dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
@@ -2343,6 +2379,75 @@ dlra_status dlra_kstep(const dlra_kstep_args* args) {
     s = DLRA_ERR_CUDA;
   }
   return (dlra_status)s;
+}
+
+dlra_status dlra_stencil_gram(const dlra_stencil_gram_args* a) {
+  using namespace dlra;
+  if (!a) {
+    set_context_free_error("null arguments");
+    return DLRA_ERR_ARG;
+  }
+  const bool two_d = a->ny == 1 && a->dy == 0.0;
+  const long long n = (long long)a->nx * a->ny * a->nz;
+  if (a->nx < 1 || a->ny < 1 || a->nz < 1 || !(a->dx > 0) || !(a->dz > 0) || !(two_d || a->dy > 0) ||
+      n >= (1LL << 31)) {
+    set_context_free_error("bad grid");
+    return DLRA_ERR_ARG;
+  }
+  if (a->na < 1 || a->na > 128 || a->nb < 1 || a->nb > 128 || a->lda < n || a->ldb < n || a->variant < 0 ||
+      a->variant > 1) {
+    set_context_free_error("need 1 <= na, nb <= 128, lda, ldb >= n and variant 0 or 1");
+    return DLRA_ERR_ARG;
+  }
+  if (!a->A || !a->B || !a->inv_rho || !a->out) {
+    set_context_free_error("null device arrays");
+    return DLRA_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)a->cuda_stream;
+  Geo g{};
+  g.nx = a->nx;
+  g.ny = a->ny;
+  g.nz = a->nz;
+  g.nxy = (long long)a->nx * a->ny;
+  g.n = n;
+  g.nact = two_d ? 2 : 3;
+  g.dirs[0] = 0;
+  g.dirs[1] = two_d ? 2 : 1;
+  g.dirs[2] = 2;
+  g.inv2d[0] = 1.0 / (2.0 * a->dx);
+  g.inv2d[1] = two_d ? 0.0 : 1.0 / (2.0 * a->dy);
+  g.inv2d[2] = 1.0 / (2.0 * a->dz);
+  const int nk = 2 * g.nact;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    set_context_free_error("cudaMalloc of the error flag failed");
+    return DLRA_ERR_OOM;
+  }
+  Tuning t;
+  t.gs_variant = a->variant;
+  TuneScope scope(&t);
+  int64_t nl = 0;
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  cudaMemsetAsync(a->out, 0, sizeof(double) * nk * a->nb * a->na, st);
+  gram_stencil<float>(st, n, a->A, a->lda, a->na, nullptr, a->B, a->ldb, a->nb, nullptr, a->inv_rho, g, a->out,
+                      a->nb, a->na, nl, err);
+  int flag = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(err);
+  if (e != cudaSuccess) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "stencil Gram failed: %s", cudaGetErrorString(e));
+    set_context_free_error(buf);
+    return DLRA_ERR_CUDA;
+  }
+  if (flag & ERR_TIMEOUT) {
+    set_context_free_error("stencil Gram: a tensor-core wait ran out");
+    return DLRA_ERR_TIMEOUT;
+  }
+  return DLRA_OK;
 }
 
 int64_t dlra_launch_count(const dlra_ctx* ctx) { return ctx ? ctx->launches : 0; }

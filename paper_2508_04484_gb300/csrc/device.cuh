@@ -112,6 +112,26 @@ __device__ __forceinline__ void stencil_values(const T* __restrict__ col, const 
   }
 }
 
+// stencil_values with the direction list fixed at compile time (x, y, z for NACT = 3; x, z for
+// an x-z slab), so that no array of the Geo argument is indexed at run time
+template <typename T, int TT, int NACT>
+__device__ __forceinline__ void stencil_values_c(const T* __restrict__ col, const int* sOff, const T* sR, int t,
+                                                 const Geo& g, T* out) {
+  const T v0 = col[0] * sR[t];
+#pragma unroll
+  for (int da = 0; da < NACT; ++da) {
+    const int d = NACT == 3 ? da : (da == 0 ? 0 : 2);
+    const int b = 1 + 4 * d;
+    const T inv = T(g.inv2d[d]);
+    const T vm1 = col[sOff[b * TT + t]] * sR[b * TT + t];
+    const T vm2 = col[sOff[(b + 1) * TT + t]] * sR[(b + 1) * TT + t];
+    const T vp1 = col[sOff[(b + 2) * TT + t]] * sR[(b + 2) * TT + t];
+    const T vp2 = col[sOff[(b + 3) * TT + t]] * sR[(b + 3) * TT + t];
+    out[2 * da] = (T(-3) * v0 + T(4) * vm1 - vm2) * inv;
+    out[2 * da + 1] = (T(3) * v0 - T(4) * vp1 + vp2) * inv;
+  }
+}
+
 __device__ __forceinline__ int dev_dim(const int* p, int cap) {
   if (p == nullptr) return cap;
   int v = *p;
@@ -717,7 +737,7 @@ __global__ void __launch_bounds__(512) gram_stencil_kernel(long long rows, const
       long long rr = r0 + t;
       T sv[NK];
       if (rr < rows && b < Bact) {
-        stencil_values<T, GS_TC>(B + (long long)b * ldb + rr, sOff, sR, t, g, sv);
+        stencil_values_c<T, GS_TC, NACT>(B + (long long)b * ldb + rr, sOff, sR, t, g, sv);
       } else {
 #pragma unroll
         for (int k = 0; k < NK; ++k) sv[k] = T(0);

@@ -111,6 +111,16 @@ void launch_dot(cudaStream_t st, const double* g, const double* a, const double*
 // transpose each of nk column-major n2 x n2 blocks in place
 void launch_transpose_blocks(cudaStream_t st, double* G, int n2, int nk);
 
+// Stencil Gram on the tensor cores (FP32): out[(k ldj + b) ldo + a] += sum_i A(i, a)
+// D_k(rho^-1 B(:, b))(i) for a < dim(adim, na), b < dim(bdim, nb); out accumulates (FP64
+// atomics). Needs na <= 128 and rows < 2^31 (gram_stencil_tc_supported). A wait that runs out
+// sets ERR_TIMEOUT in *err and leaves out without this launch's terms.
+struct Geo;
+bool gram_stencil_tc_supported(int na, long long rows);
+void launch_gram_stencil_tc(cudaStream_t st, long long rows, const float* A, long long lda, int na, const int* adim,
+                            const float* B, long long ldb, int nb, const int* bdim, const float* inv_rho,
+                            const Geo& g, double* out, int ldj, long long ldo, int waves_x2, int* err);
+
 // Work-space bytes of one stand-alone K-step (see dlra_kstep) and the step itself on
 // caller-provided device work space of at least that many bytes.
 size_t kstep_scratch_bytes(long long n, int r, int nact);

@@ -63,6 +63,15 @@ class dlra_kstep_args(C.Structure):
                 ("cuda_stream", C.c_void_p)]
 
 
+class dlra_stencil_gram_args(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("na", C.c_int32), ("nb", C.c_int32),
+                ("A", C.c_void_p), ("lda", C.c_int64), ("B", C.c_void_p), ("ldb", C.c_int64),
+                ("inv_rho", C.c_void_p), ("out", C.c_void_p), ("variant", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
 # names, argument types and return type of every entry point of include/dlra.h
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -89,10 +98,12 @@ SIGNATURES = {
     "dlra_set_tensor_cores": ([_P, C.c_int32], C.c_int),
     "dlra_set_graphs": ([_P, C.c_int32], C.c_int),
     "dlra_set_adjoint_store": ([_P, C.c_int32], C.c_int),
+    "dlra_set_stencil_gram_kernel": ([_P, C.c_int32], C.c_int),
     "dlra_set_profiling": ([_P, C.c_int32], C.c_int),
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
+    "dlra_stencil_gram": ([C.POINTER(dlra_stencil_gram_args)], C.c_int),
     "dlra_launch_count": ([_P], C.c_int64),
     "dlra_last_error": ([_P], C.c_char_p),
     "dlra_destroy": ([_P], None),
@@ -324,17 +335,22 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(13)
+    rep = np.zeros(15)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
-                stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])),
+                stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), stencil_gram_tc_ms=rep[13],
                 stage_variant=("per-cell FMA", "tensor cores", "brick FMA")[int(rep[9])],
-                gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0)
+                gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
+                stencil_gram_kernel=("FMA", "tensor cores")[int(rep[14])])
 
 
 def dlra_set_stage_kernel(ctx, variant: int):
     _check(ctx, load().dlra_set_stage_kernel(ctx, int(variant)))
+
+
+def dlra_set_stencil_gram_kernel(ctx, variant: int):
+    _check(ctx, load().dlra_set_stencil_gram_kernel(ctx, int(variant)))
 
 
 def dlra_set_tensor_cores(ctx, enable=True):
@@ -386,6 +402,32 @@ def dlra_kstep_noalloc(args):
     st = load().dlra_kstep_noalloc(C.byref(args))
     if st != DLRA_OK:
         raise DlraError(st, load().dlra_last_error(None).decode())
+
+
+def dlra_stencil_gram(args):
+    st = load().dlra_stencil_gram(C.byref(args))
+    if st != DLRA_OK:
+        raise DlraError(st, load().dlra_last_error(None).decode())
+
+
+def stencil_gram(grid, spacing, A, B, inv_rho, variant=0):
+    """G[k, b, a] = sum_i A[i, a] D_k(rho^-1 B[:, b])[i] for device FP32 tensors A (n x na) and
+    B (n x nb), column-major (A[:, a] contiguous: pass A as an (na, n) row-major tensor's
+    transpose or as the .T of a contiguous tensor); returns an FP64 device tensor (nk, nb, na)."""
+    import torch
+    nx, ny, nz = grid
+    dx, dy, dz = spacing
+    two_d = ny == 1 and dy == 0.0
+    nk = 4 if two_d else 6
+    n = nx * ny * nz
+    assert A.shape[0] == n and B.shape[0] == n and A.stride(0) == 1 and B.stride(0) == 1
+    na, nb = A.shape[1], B.shape[1]
+    out = torch.empty((nk, nb, na), dtype=torch.float64, device=A.device)
+    args = dlra_stencil_gram_args(nx, ny, nz, dx, dy, dz, na, nb, A.data_ptr(), A.stride(1), B.data_ptr(),
+                                  B.stride(1), inv_rho.data_ptr(), out.data_ptr(), int(variant),
+                                  torch.cuda.current_stream(A.device).cuda_stream)
+    dlra_stencil_gram(args)
+    return out
 
 
 def dlra_launch_count(ctx) -> int:
@@ -494,6 +536,10 @@ class Solver:
     def set_stage_kernel(self, variant):
         """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA."""
         dlra_set_stage_kernel(self.ctx, variant)
+
+    def set_stencil_gram_kernel(self, variant):
+        """0 FMA, 1 tensor cores (FP32 path)."""
+        dlra_set_stencil_gram_kernel(self.ctx, variant)
 
     def set_tensor_cores(self, enable=True):
         """Run the streaming stage on the tcgen05 tensor cores (FP32-mixed path)."""

@@ -1,0 +1,112 @@
+"""GPU parity of the stencil Gram G_k[a][b] = sum_i A(i, a) D_k(rho^-1 B(:, b))(i), the Galerkin
+blocks of the streaming operator in the L-step and S-step (Sec. 3.3.2), through the stand-alone
+C-ABI entry point dlra_stencil_gram: the FMA kernel and the tensor-core kernel (tcgen05 kind::tf32
+with high/low splits) against the oracle's stencils (oracle/grid.py apply_D) in FP64 on the same
+FP32 inputs."""
+import numpy as np
+import pytest
+
+from oracle import grid as OG
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_04484_gb300 import build
+    build.build()
+
+
+def _oracle_gram(dims, spacing, A, B, inv_rho):
+    two_d = dims[1] == 1 and spacing[1] == 0.0
+    dirs = (0, 2) if two_d else (0, 1, 2)
+    V = inv_rho[:, None] * B
+    G = []
+    for d in dirs:
+        for sign in (-1, +1):
+            G.append(OG.apply_D(V, dims, d, sign, spacing[d]).T @ A)
+    return np.array(G)
+
+
+def _case(dims, spacing, na, nb, seed, lda_pad=0):
+    rng = np.random.default_rng(seed)
+    n = dims[0] * dims[1] * dims[2]
+    A = rng.standard_normal((na, n + lda_pad)).astype(np.float32)
+    B = rng.standard_normal((nb, n + lda_pad)).astype(np.float32)
+    inv_rho = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    return A, B, inv_rho
+
+
+def _gpu_gram(dims, spacing, A, B, inv_rho, variant):
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    dev = torch.device("cuda", 0)
+    n = inv_rho.shape[0]
+    # column-major n x na with leading dimension A.shape[1]: the transpose of a row-major (na, lda)
+    At = torch.tensor(A, device=dev).T[:n]
+    Bt = torch.tensor(B, device=dev).T[:n]
+    r = torch.tensor(inv_rho, device=dev)
+    G = D.stencil_gram(dims, spacing, At, Bt, r, variant=variant)
+    torch.cuda.synchronize()
+    return G.cpu().numpy()
+
+
+# (grid, spacing, padding of the leading dimensions)
+SHAPES = [
+    ((13, 7, 9), (0.2, 0.25, 0.3), 3),   # 819 cells: 25 full 32-cell chunks and a ragged one
+    ((37, 1, 21), (0.2, 0.0, 0.25), 3),  # x-z slab, nk = 4
+    ((12, 5, 7), (0.2, 0.25, 0.3), 4),   # x-extent a multiple of 4 (float4 stencil loads), 420 cells
+    ((20, 1, 9), (0.2, 0.0, 0.25), 8),   # the same on a slab, 180 cells
+]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("na,nb", [(20, 20), (40, 40), (7, 5), (64, 50), (128, 128), (16, 43)])
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_stencil_gram_matches_oracle(shape, na, nb, variant):
+    dims, spacing, pad = SHAPES[shape]
+    A, B, inv_rho = _case(dims, spacing, na, nb, seed=10 + na + nb, lda_pad=pad)
+    n = inv_rho.shape[0]
+    Go = _oracle_gram(dims, spacing, A[:, :n].T.astype(np.float64), B[:, :n].T.astype(np.float64),
+                      inv_rho.astype(np.float64))
+    G = _gpu_gram(dims, spacing, A, B, inv_rho, variant)
+    assert G.shape == Go.shape
+    scale = np.abs(Go).max()
+    # FP32 sums of a few hundred terms of size ~10: a few 1e-6 of the largest entry
+    assert np.abs(G - Go).max() <= 3e-6 * scale
+    for k in range(Go.shape[0]):
+        assert np.linalg.norm(G[k] - Go[k]) <= 2e-6 * np.linalg.norm(Go[k])
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_stencil_gram_full_size_64cube(variant):
+    # the shape of the augmented-basis Gram of the 64^3 workload: n2 = 40 columns on both sides
+    dims, spacing = (64, 64, 64), (0.2, 0.2, 0.2)
+    A, B, inv_rho = _case(dims, spacing, 40, 40, seed=5)
+    Go = _oracle_gram(dims, spacing, A.T.astype(np.float64), B.T.astype(np.float64), inv_rho.astype(np.float64))
+    G = _gpu_gram(dims, spacing, A, B, inv_rho, variant)
+    # 262144-term sums: FP32 within a block, FP64 across blocks
+    for k in range(Go.shape[0]):
+        assert np.linalg.norm(G[k] - Go[k]) <= 2e-5 * np.linalg.norm(Go[k])
+
+
+def test_stencil_gram_same_basis_is_the_solver_shape():
+    # A = B (the L-step and S-step case): both kernels agree to FP32 round-off
+    dims, spacing = (16, 16, 16), (0.25, 0.25, 0.25)
+    A, _, inv_rho = _case(dims, spacing, 24, 1, seed=8)
+    G0 = _gpu_gram(dims, spacing, A, A, inv_rho, 0)
+    G1 = _gpu_gram(dims, spacing, A, A, inv_rho, 1)
+    assert np.linalg.norm(G1 - G0) <= 2e-6 * np.linalg.norm(G0)
+
+
+def test_stencil_gram_rejects_bad_arguments():
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    dev = torch.device("cuda", 0)
+    X = torch.zeros((129, 64), dtype=torch.float32, device=dev).T   # 64 cells x 129 columns
+    r = torch.ones(64, dtype=torch.float32, device=dev)
+    with pytest.raises(D.DlraError):
+        D.stencil_gram((4, 4, 4), (0.1, 0.1, 0.1), X, X, r)

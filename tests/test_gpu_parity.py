@@ -168,6 +168,28 @@ def test_stage_kernel_variants_match_oracle(case, variant):
     assert rel_l2(doses[1], dose) < 1e-3
 
 
+@pytest.mark.parametrize("case", ["slab", "cube"])
+def test_tensor_core_stencil_gram_matches_oracle(case):
+    # the L-step and S-step Galerkin blocks on the tensor cores, in a whole solve
+    if case == "slab":
+        cfg, mats, w, beams = _slab(precision=WL.FP32_MIXED)
+        mode, kw = OP.FIXED, dict(rank=6)
+    else:
+        cfg, mats, w, beams = _cube()
+        mode, kw = OP.ADAPTIVE, dict(tol=1e-3, r_max=12)
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    dose, res = oracle_dlra(prob, src, mode, **kw)
+    doses = []
+    for v in (0, 1):
+        s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=WL.FP32_MIXED)
+        s.set_stencil_gram_kernel(v)
+        doses.append(s.run())
+        s.close()
+    assert rel_l2(doses[1], doses[0]) < 1e-5
+    assert rel_l2(doses[1], dose) < 1e-3
+
+
 def test_brick_stage_fp64_matches_oracle():
     cfg, mats, w, beams = _slab(precision=WL.FP64)
     prob = oracle_problem(cfg, mats, w)
