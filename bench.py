@@ -45,6 +45,11 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
+    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2], default=None,
+                   help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick), "
+                        "set after the autotuner")
+    p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1], default=None,
+                   help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores), set after the autotuner")
     p.add_argument("--replicas", action="store_true",
                    help="with several ranks, solve the whole multi-beam workload on every rank")
     p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
@@ -61,18 +66,31 @@ def _workload(name=WORKLOAD):
     return getattr(WL, name)()
 
 
+KSTAGE_BEGIN = "template <typename T, int RM, int NACT>\n__global__ void __launch_bounds__(128) kstage_kernel("
+KSTAGE_END = "// Cell bricks of the staged streaming stage"
+
+
+def kstage_source_sha256():
+    """sha256 of the source text of kstage_kernel (its template line to the next section), or
+    None if the markers are not found."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", "device.cuh")).read()
+    i, j = src.find(KSTAGE_BEGIN), src.find(KSTAGE_END)
+    if i < 0 or j < i:
+        return None
+    return hashlib.sha256(src[i:j].encode()).hexdigest()
+
+
 def _stage_traffic():
     """DRAM bytes per launch of the fused streaming stage from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
-    import hashlib
+    or None when the kernel's source changed since that capture."""
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
-    src = os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", "device.cuh")
     if not os.path.exists(path):
         return None, None
     with open(path) as f:
         d = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("device_cuh_sha256") != h:
+    h = kstage_source_sha256()
+    if h is None or d.get("kstage_source_sha256") != h:
         return None, "kernel changed since the capture"
     return float(d["dram_bytes_per_launch"]), d.get("capture", "")
 
@@ -296,6 +314,10 @@ def main():
             MG.reduce_dose(dose)
 
     tuned = solver.autotune() if not args.no_autotune else None
+    if args.stage_kernel is not None:
+        solver.set_stage_kernel(args.stage_kernel)
+    if args.stencil_gram_kernel is not None:
+        solver.set_stencil_gram_kernel(args.stencil_gram_kernel)
     use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
     solver.set_graphs(use_graphs)
     for _ in range(args.warmup):

@@ -211,6 +211,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1) gram_stencil_tc_kernel(
   const long long nchunks = (rows + GT_TC - 1) / GT_TC;
   const int ag = NP >> 3;         // 8-row groups of a
   const int nbq = (nb + 3) >> 2;  // column quads of b
+  // float4 path: the last warp only issues the MMAs (it forms no stencil values), so that the
+  // issue never delays a staging warp; the other warps take the stencil items
+  const int nbo = (nb + 7) >> 3;
+  const int sw = VEC ? NW - 1 : NW;  // staging warps
+  const int issuer = VEC ? (NW - 1) * 32 : 0;
   // S staging: warp w covers cells t = 8 (w % 4) + lane / 4 and the column quads w / 4, w / 4 + 4, ...
   const int t = 8 * (warp & 3) + (lane >> 2);
   const int bq0 = warp >> 2;
@@ -256,9 +261,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1) gram_stencil_tc_kernel(
       }
     }
     // float4 stencil path: this warp's first item is loaded before the wait
-    const int nbo = (nb + 7) >> 3;
     QuadIn<NACT> qin;
-    if (VEC && warp < 2 * nbo) qin.load(warp, nb, Bact, r0, rows, B, ldb, inv_rho, g, lane);
+    if (VEC && warp < sw && warp < 2 * nbo) qin.load(warp, nb, Bact, r0, rows, B, ldb, inv_rho, g, lane);
     // the buffer is free once the MMAs of chunk u - 2 (its previous use) are done
     if (u >= 2 && !tc::mbar_wait(&mbar[bsel], (uint32_t)(((u - 2) >> 1) & 1), tc::kWaitLimit)) alive = false;
 #pragma unroll
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) gram_stencil_tc_kernel(
       // float4 loads of the column and of rho^-1 give its 13-point stencils, and each of the nk
       // values of the quad is one 16-byte store (four consecutive K of a core-matrix row).
       // Item (column octet, half of the chunk): lanes = 8 columns x 4 quads.
-      for (int it = warp; it < 2 * nbo; it += NW) {
+      for (int it = warp; warp < sw && it < 2 * nbo; it += sw) {
         if (it != warp) qin.load(it, nb, Bact, r0, rows, B, ldb, inv_rho, g, lane);
         if (!qin.store) continue;
         float sv[NK][4];
@@ -342,21 +346,22 @@ __global__ void __launch_bounds__(GT_THREADS, 1) gram_stencil_tc_kernel(
       alive = false;
       break;
     }
-    if (tid == 0) {
+    if (tid == issuer) {
       tc::fence_after();
-      const uint32_t ah = tc::su32(Ahi), al = tc::su32(Alo);
+      // a K-slice further is a fixed byte offset: added to the descriptors' address field
+      // (addresses stay below 256 KB, so the 14-bit field never carries)
+      const uint64_t dAh = tc::smem_desc(tc::su32(Ahi), aLBO, 128), dAl = tc::smem_desc(tc::su32(Alo), aLBO, 128);
       for (int mt = 0; mt < MT; ++mt) {
-        const uint32_t sh = tc::su32(Shi + mt * 128 * GT_TC), sl = tc::su32(Slo + mt * 128 * GT_TC);
+        const uint64_t dSh = tc::smem_desc(tc::su32(Shi + mt * 128 * GT_TC), sLBO, 128);
+        const uint64_t dSl = tc::smem_desc(tc::su32(Slo + mt * 128 * GT_TC), sLBO, 128);
         const uint32_t d = tmem + (uint32_t)(mt * NP);
 #pragma unroll
         for (int ks = 0; ks < GT_TC / 8; ++ks) {
-          const uint32_t so = ks * 2 * sLBO, ao = ks * 2 * aLBO;
-          const uint64_t dSh = tc::smem_desc(sh + so, sLBO, 128), dSl = tc::smem_desc(sl + so, sLBO, 128);
-          const uint64_t dAh = tc::smem_desc(ah + ao, aLBO, 128), dAl = tc::smem_desc(al + ao, aLBO, 128);
+          const uint64_t so = (uint64_t)((ks * 2 * sLBO) >> 4), ao = (uint64_t)((ks * 2 * aLBO) >> 4);
           const uint32_t acc = (u == 0 && ks == 0) ? 0u : 1u;
-          tc::mma_tf32(d, dSh, dAh, idesc, acc);
-          tc::mma_tf32(d, dSh, dAl, idesc, 1u);
-          tc::mma_tf32(d, dSl, dAh, idesc, 1u);
+          tc::mma_tf32(d, dSh + so, dAh + ao, idesc, acc);
+          tc::mma_tf32(d, dSh + so, dAl + ao, idesc, 1u);
+          tc::mma_tf32(d, dSl + so, dAh + ao, idesc, 1u);
         }
       }
       tc::mma_commit(&mbar[bsel]);
