@@ -6,6 +6,7 @@
 // one contiguous vector per column. Small matrices are FP64 column-major.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 namespace dlra {
@@ -441,9 +442,15 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
   T inv2[NACT];
 #pragma unroll
   for (int da = 0; da < NACT; ++da) inv2[da] = T(g.inv2d[(NACT == 3) ? da : (da == 0 ? 0 : 2)]);
+  // FP32: the r x r mix in packed two-lane FMAs (fma.rn.f32x2, each lane rounded as a scalar FMA),
+  // half the FMA instructions of the issue-bound loop
+  constexpr bool F2 = std::is_same<T, float>::value;
   T acc[RM];
+  float2 acc2[F2 ? RM / 2 : 1];
 #pragma unroll
   for (int c = 0; c < RM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int c = 0; c < (F2 ? RM / 2 : 1); ++c) acc2[c] = make_float2(0.f, 0.f);
   for (int c = 0; c < r; ++c) {
     const T* col = vin + (long long)c * ld + i;
     T v[NP];
@@ -465,15 +472,32 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
     const T* Pc = sP + (long long)c * NK * RM;
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
+      if constexpr (F2) {
+        const float2 s2 = make_float2(sv[k], sv[k]);
 #pragma unroll
-      for (int cp = 0; cp < RM; cp += 4) {
-        T p4[4];
-        Vec4<T>::load(Pc + k * RM + cp, p4);
-        acc[cp] += sv[k] * p4[0];
-        acc[cp + 1] += sv[k] * p4[1];
-        acc[cp + 2] += sv[k] * p4[2];
-        acc[cp + 3] += sv[k] * p4[3];
+        for (int cp = 0; cp < RM; cp += 4) {
+          const float4 p = *reinterpret_cast<const float4*>(Pc + k * RM + cp);
+          acc2[cp / 2] = __ffma2_rn(s2, make_float2(p.x, p.y), acc2[cp / 2]);
+          acc2[cp / 2 + 1] = __ffma2_rn(s2, make_float2(p.z, p.w), acc2[cp / 2 + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int cp = 0; cp < RM; cp += 4) {
+          T p4[4];
+          Vec4<T>::load(Pc + k * RM + cp, p4);
+          acc[cp] += sv[k] * p4[0];
+          acc[cp + 1] += sv[k] * p4[1];
+          acc[cp + 2] += sv[k] * p4[2];
+          acc[cp + 3] += sv[k] * p4[3];
+        }
       }
+    }
+  }
+  if constexpr (F2) {
+#pragma unroll
+    for (int c = 0; c < RM / 2; ++c) {
+      acc[2 * c] = acc2[c].x;
+      acc[2 * c + 1] = acc2[c].y;
     }
   }
   const T ir0 = inv_rho[i];
@@ -654,24 +678,46 @@ __global__ void __launch_bounds__(128) apply_kernel(long long rows, const T* __r
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
+  // FP32: packed two-lane FMAs (fma.rn.f32x2), as in the streaming stage
+  constexpr bool F2 = std::is_same<T, float>::value;
   T acc[NM];
+  float2 acc2[F2 ? NM / 2 : 1];
 #pragma unroll
   for (int c = 0; c < NM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int c = 0; c < (F2 ? NM / 2 : 1); ++c) acc2[c] = make_float2(0.f, 0.f);
   const T* a = A + i;
   T cur = Qa > 0 ? a[0] : T(0);
   for (int q = 0; q < Qa; ++q) {
     const T nxt = q + 1 < Qa ? a[(long long)(q + 1) * lda] : T(0);
     const T* mrow = sM + q * NM;
+    if constexpr (F2) {
+      const float2 c2 = make_float2(cur, cur);
 #pragma unroll
-    for (int c = 0; c < NM; c += 4) {
-      T m4[4];
-      Vec4<T>::load(mrow + c, m4);
-      acc[c] += cur * m4[0];
-      acc[c + 1] += cur * m4[1];
-      acc[c + 2] += cur * m4[2];
-      acc[c + 3] += cur * m4[3];
+      for (int c = 0; c < NM; c += 4) {
+        const float4 m = *reinterpret_cast<const float4*>(mrow + c);
+        acc2[c / 2] = __ffma2_rn(c2, make_float2(m.x, m.y), acc2[c / 2]);
+        acc2[c / 2 + 1] = __ffma2_rn(c2, make_float2(m.z, m.w), acc2[c / 2 + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NM; c += 4) {
+        T m4[4];
+        Vec4<T>::load(mrow + c, m4);
+        acc[c] += cur * m4[0];
+        acc[c + 1] += cur * m4[1];
+        acc[c + 2] += cur * m4[2];
+        acc[c + 3] += cur * m4[3];
+      }
     }
     cur = nxt;
+  }
+  if constexpr (F2) {
+#pragma unroll
+    for (int c = 0; c < NM / 2; ++c) {
+      acc[2 * c] = acc2[c].x;
+      acc[2 * c + 1] = acc2[c].y;
+    }
   }
   const T ir = V ? inv_rho[i] : T(0);
 #pragma unroll
