@@ -45,8 +45,8 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
-    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2], default=None,
-                   help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick), "
+    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3], default=None,
+                   help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs), "
                         "set after the autotuner")
     p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1], default=None,
                    help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores), set after the autotuner")
@@ -66,31 +66,46 @@ def _workload(name=WORKLOAD):
     return getattr(WL, name)()
 
 
-KSTAGE_BEGIN = "template <typename T, int RM, int NACT>\n__global__ void __launch_bounds__(128) kstage_kernel("
-KSTAGE_END = "// Cell bricks of the staged streaming stage"
+# streaming-stage kernels by variant: name and the markers of their source text in device.cuh
+# (the DRAM traffic of a capture is reported only while that text is unchanged)
+STAGE_KERNELS = {
+    0: ("kstage_kernel", "template <typename T, int RM, int NACT>\n__global__ void __launch_bounds__(128) kstage_kernel(",
+        "// The streaming stage of kstage_kernel on the FP32 path with two"),
+    1: ("kstage_tc_kernel", None, None),
+    2: ("kstage_brick_kernel", "// Cell bricks of the staged streaming stage", None),
+    3: ("kstage_pair_kernel", "// The streaming stage of kstage_kernel on the FP32 path with two",
+        "// Cell bricks of the staged streaming stage"),
+}
+STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3}
 
 
-def kstage_source_sha256():
-    """sha256 of the source text of kstage_kernel (its template line to the next section), or
-    None if the markers are not found."""
+def stage_source_sha256(variant):
+    """sha256 of the source text of a streaming-stage kernel, or None without markers."""
     import hashlib
+    _, begin, end = STAGE_KERNELS[variant]
+    if begin is None or end is None:
+        return None
     src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", "device.cuh")).read()
-    i, j = src.find(KSTAGE_BEGIN), src.find(KSTAGE_END)
+    i = src.find(begin)
+    j = src.find(end, i + 1) if i >= 0 else -1
     if i < 0 or j < i:
         return None
     return hashlib.sha256(src[i:j].encode()).hexdigest()
 
 
-def _stage_traffic():
-    """DRAM bytes per launch of the fused streaming stage from the committed ncu summary,
-    or None when the kernel's source changed since that capture."""
+def _stage_traffic(variant):
+    """DRAM bytes per launch of the streaming-stage kernel in use from the committed ncu summary,
+    or None when there is none or the kernel's source changed since that capture."""
+    name = STAGE_KERNELS[variant][0]
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
     if not os.path.exists(path):
         return None, None
     with open(path) as f:
-        d = json.load(f)
-    h = kstage_source_sha256()
-    if h is None or d.get("kstage_source_sha256") != h:
+        d = json.load(f).get("kernels", {}).get(name)
+    if d is None:
+        return None, f"no capture of {name}"
+    h = stage_source_sha256(variant)
+    if h is None or d.get("source_sha256") != h:
         return None, "kernel changed since the capture"
     return float(d["dram_bytes_per_launch"]), d.get("capture", "")
 
@@ -383,8 +398,12 @@ def main():
     tfs = avg_flops / (avg_launch_ms / 1000.0) / 1e12
     frac_hbm = gbs / hbm_peak
     frac_alu = tfs / fp32_peak
-    traffic, traffic_note = _stage_traffic()
-    kname = "kstage_kernel (fused RK4 streaming stage: stencil + r x r mix)"
+    variant = args.stage_kernel if args.stage_kernel is not None else (
+        STAGE_NAMES.get(tuned["stage_variant"], 0) if tuned else 0)
+    if variant == 3 and cfg["nx"] % 2:
+        variant = 0
+    traffic, traffic_note = _stage_traffic(variant)
+    kname = f"{STAGE_KERNELS[variant][0]} (fused RK4 streaming stage: stencil + r x r mix)"
     if frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
                 "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,

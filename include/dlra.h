@@ -215,21 +215,25 @@ dlra_status dlra_backward(dlra_ctx* ctx, const double* dL_de, int32_t in_on_devi
 dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
 
 /* Autotuner: times the launch variants of the heavy cell-side kernels on this context's work
- * space (filled with synthetic values at full rank capacity) and keeps the fastest: the
+ * space (filled with synthetic values at full rank capacity; the streaming stages one launch at
+ * a time after a 256 MB write, i.e. with a cold L2 as inside a solve; allocates those 256 MB
+ * for the duration of the call) and keeps the fastest: the
  * streaming stage per cell with FMA, on the tensor cores (FP32 path) or per brick with FMA and
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel). Needs materials and a beam; synchronises; drops captured graphs. report (optional,
- * 15 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 per cell, 1 tensor cores, 2 brick), Gram block
- * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram
- * (-1 where not applicable) and the chosen stencil-Gram kernel (0 FMA, 1 tensor cores). */
+ * 16 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 per cell, 1 tensor cores, 2 brick, 3 cell
+ * pairs), Gram block target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core
+ * stencil Gram, the chosen stencil-Gram kernel (0 FMA, 1 tensor cores) and ms of the cell-pair
+ * stage (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
  * 1 the tensor-core kernel of dlra_set_tensor_cores (FP32 path; the FMA kernel on FP64),
- * 2 one block per 256-cell brick with the stencil inputs staged in shared memory. Same results
- * up to rounding; dlra_autotune picks among them. */
+ * 2 one block per 256-cell brick with the stencil inputs staged in shared memory, 3 two
+ * x-adjacent cells per thread with packed FP32x2 FMAs (FP32 path with nx even; else variant 0).
+ * Same results up to rounding; dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):

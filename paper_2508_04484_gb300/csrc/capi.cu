@@ -265,6 +265,15 @@ void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, 
     return;
   }
   if constexpr (sizeof(T) == 4) {
+    if (variant == 3 && g.nx % 2 == 0) {
+      // FP32 path: two x-adjacent cells per thread
+      const size_t smem = (size_t)2 * NACT * RM * RM * sizeof(float);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kstage_pair_kernel<RM, NACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kstage_pair_kernel<RM, NACT><<<nblk(n / 2, 128), 128, smem, st>>>(vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
+                                                                        beta, last);
+      return;
+    }
     if (variant == 1) {
       // FP32 path on request: the r x r mix on the tensor cores (3xTF32)
       const size_t smem = kstage_tc_smem<NACT, RM>();
@@ -1719,11 +1728,11 @@ dlra_status backward_t(dlra_ctx* ctx, double* dbeta_host, double* dw_out, int ou
 }
 
 // Times the launch variants of the heavy n-side kernels on lane 0's work space filled with
-// synthetic values (rank = capacity) and keeps the fastest. report (optional, 15 doubles): ms of
+// synthetic values (rank = capacity) and keeps the fastest (streaming stages with a cold L2). report (optional, 16 doubles): ms of
 // the FMA / tensor-core streaming stage, of the Gram reduction at 608 / 1216 / 2432 / 4864
 // target blocks, of the stencil Gram at 0.5 / 1 / 2 waves, then the chosen stage variant,
 // Gram block target and stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core
-// stencil Gram and the chosen stencil-Gram kernel.
+// stencil Gram, the chosen stencil-Gram kernel and ms of the cell-pair stage.
 template <typename T>
 dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   Engine<T> E{ctx};
@@ -1758,17 +1767,43 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
     cudaEventElapsedTime(&ms, e0, e1);
     return (double)ms / 5.0;
   };
+  // the streaming stage reads most of its inputs from DRAM inside a solve (the other chains of
+  // the step evict them from L2): its variants are timed one launch at a time after a write of
+  // 256 MB, which a warm loop of launches would misjudge
+  const size_t flush_bytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  CK(cudaMalloc(&flush, flush_bytes));
+  auto time_cold_ms = [&](auto&& launch) {
+    launch();
+    double tot = 0.0;
+    for (int w = 0; w < 5; ++w) {
+      cudaMemsetAsync(flush, w, flush_bytes, st);
+      cudaEventRecord(e0, st);
+      launch();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    return tot / 5.0;
+  };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[15] = {0};
-  // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA
-  double stage_ms[3];
-  for (int v = 0; v < 3; ++v) {
-    if (v == 1 && sizeof(T) != 4) {
+  double rep[16] = {0};
+  // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
+  // path, nx even)
+  double stage_ms[4];
+  for (int v = 0; v < 4; ++v) {
+    if ((v == 1 || v == 3) && sizeof(T) != 4) {
       stage_ms[v] = -1.0;
       continue;
     }
-    stage_ms[v] = time_ms([&] {
+    if (v == 3 && ctx->geo.nx % 2 != 0) {
+      stage_ms[v] = -1.0;
+      continue;
+    }
+    stage_ms[v] = time_cold_ms([&] {
       kstage<T>(RB, st, E.P(L.Kb[1]), E.P(L.Kb[0]), E.P(L.Kb[0]), E.P(L.Kb[2]), n, E.P(ctx->inv_rho), ctx->geo,
                 E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v);
     });
@@ -1807,9 +1842,10 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
+  cudaFree(flush);
   Tuning best = ctx->tun;
   int sv = 0;
-  for (int v = 1; v < 3; ++v)
+  for (int v = 1; v < 4; ++v)
     if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
   best.kstage_variant = sv;
   int bi = 0;
@@ -1825,6 +1861,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   rep[14] = best.gs_variant;
   rep[9] = best.kstage_variant;
   rep[12] = stage_ms[2];
+  rep[15] = stage_ms[3];
   rep[10] = best.gram_blocks;
   rep[11] = best.gs_waves_x2;
   ctx->tun = best;
@@ -2205,7 +2242,7 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 2) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0, 1, 2 or 3");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;

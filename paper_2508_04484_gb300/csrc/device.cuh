@@ -521,6 +521,119 @@ __global__ void __launch_bounds__(128) kstage_kernel(const T* __restrict__ vin, 
   }
 }
 
+// The streaming stage of kstage_kernel on the FP32 path with two x-adjacent cells per thread
+// (cells 2t and 2t + 1 of a row; nx even): the two cells share four of their x-neighbour loads
+// and every P value read from shared memory feeds both cells' packed two-lane FMAs. Same modes
+// and outputs as kstage_kernel.
+template <int RM, int NACT>
+__global__ void __launch_bounds__(128) kstage_pair_kernel(const float* __restrict__ vin, const float* __restrict__ y,
+                                                          float* __restrict__ yout, float* __restrict__ vout,
+                                                          long long ld, const float* __restrict__ inv_rho, Geo g,
+                                                          const float* __restrict__ Pst,
+                                                          const int* __restrict__ rdim, float beta, int last) {
+  constexpr int NK = 2 * NACT;
+  extern __shared__ __align__(16) unsigned char raw[];
+  float* sP = reinterpret_cast<float*>(raw);
+  const int r = dev_dim(rdim, RM);
+  for (int e = threadIdx.x; e < NK * RM * r; e += blockDim.x) sP[e] = Pst[e];
+  __syncthreads();
+  const long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= g.n) return;
+  const int ii = (int)i, nxy = (int)g.nxy;
+  const int iz = ii / nxy, rem = ii - iz * nxy;
+  const int iy = rem / g.nx, ix = rem - iy * g.nx;
+  // x: cells ix - 2 .. ix + 3 (offsets -2 .. 3 from cell i); y and z: -1, -2, +1, +2
+  int xo[6];
+  unsigned xv = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int c = ix - 2 + d;
+    const bool ok = c >= 0 && c < g.nx;
+    xo[d] = ok ? d - 2 : 0;
+    xv |= ok ? (1u << d) : 0u;
+  }
+  int yo[4], zo[4];
+  unsigned yzv = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int delta = q == 0 ? -1 : (q == 1 ? -2 : (q == 2 ? 1 : 2));
+    const bool oky = NACT == 3 && iy + delta >= 0 && iy + delta < g.ny;
+    const bool okz = iz + delta >= 0 && iz + delta < g.nz;
+    yo[q] = oky ? delta * g.nx : 0;
+    zo[q] = okz ? delta * nxy : 0;
+    yzv |= (oky ? 1u << q : 0u) | (okz ? 1u << (4 + q) : 0u);
+  }
+  float inv2[NACT];
+#pragma unroll
+  for (int da = 0; da < NACT; ++da) inv2[da] = (float)g.inv2d[(NACT == 3) ? da : (da == 0 ? 0 : 2)];
+  float2 acc2[2][RM / 2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < RM / 2; ++c) acc2[h][c] = make_float2(0.f, 0.f);
+  for (int c = 0; c < r; ++c) {
+    const float* col = vin + (long long)c * ld + i;
+    float xq[6], yq[2][4], zq[2][4];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) xq[d] = (xv >> d) & 1u ? col[xo[d]] : 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        yq[h][q] = (yzv >> q) & 1u ? col[h + yo[q]] : 0.f;
+        zq[h][q] = (yzv >> (4 + q)) & 1u ? col[h + zo[q]] : 0.f;
+      }
+    float sv[2][NK];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float v0 = xq[2 + h];
+      sv[h][0] = (-3.f * v0 + 4.f * xq[1 + h] - xq[h]) * inv2[0];
+      sv[h][1] = (3.f * v0 - 4.f * xq[3 + h] + xq[4 + h]) * inv2[0];
+      if (NACT == 3) {
+        sv[h][2] = (-3.f * v0 + 4.f * yq[h][0] - yq[h][1]) * inv2[1];
+        sv[h][3] = (3.f * v0 - 4.f * yq[h][2] + yq[h][3]) * inv2[1];
+      }
+      sv[h][NK - 2] = (-3.f * v0 + 4.f * zq[h][0] - zq[h][1]) * inv2[NACT - 1];
+      sv[h][NK - 1] = (3.f * v0 - 4.f * zq[h][2] + zq[h][3]) * inv2[NACT - 1];
+    }
+    const float* Pc = sP + (long long)c * NK * RM;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const float2 s0 = make_float2(sv[0][k], sv[0][k]), s1 = make_float2(sv[1][k], sv[1][k]);
+#pragma unroll
+      for (int cp = 0; cp < RM; cp += 4) {
+        const float4 p = *reinterpret_cast<const float4*>(Pc + k * RM + cp);
+        const float2 pa = make_float2(p.x, p.y), pb = make_float2(p.z, p.w);
+        acc2[0][cp / 2] = __ffma2_rn(s0, pa, acc2[0][cp / 2]);
+        acc2[0][cp / 2 + 1] = __ffma2_rn(s0, pb, acc2[0][cp / 2 + 1]);
+        acc2[1][cp / 2] = __ffma2_rn(s1, pa, acc2[1][cp / 2]);
+        acc2[1][cp / 2 + 1] = __ffma2_rn(s1, pb, acc2[1][cp / 2 + 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long ih = i + h;
+    const float ir0 = inv_rho[ih];
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      const float a = (c & 1) ? acc2[h][c / 2].y : acc2[h][c / 2].x;
+      const long long e = (long long)c * ld + ih;
+      if (last == 2) {
+        const float lam = beta * ir0 * a;
+        vout[e] = lam;
+        yout[e] = y[e] + lam;
+      } else if (last) {
+        const float yn = y[e] + beta * a;
+        yout[e] = yn;
+        vout[e] = ir0 * yn;
+      } else {
+        vout[e] = ir0 * (y[e] + beta * a);
+      }
+    }
+  }
+}
+
 // Cell bricks of the staged streaming stage: 256 cells per block (8 x 8 x 4 in 3-D,
 // 16 x 1 x 16 in a 2-D slab) and their two-cell halo.
 template <int NACT>

@@ -335,12 +335,13 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(15)
+    rep = np.zeros(16)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
                 stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), stencil_gram_tc_ms=rep[13],
-                stage_variant=("per-cell FMA", "tensor cores", "brick FMA")[int(rep[9])],
+                stage_pair_ms=rep[15],
+                stage_variant=("per-cell FMA", "tensor cores", "brick FMA", "cell pairs")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
                 stencil_gram_kernel=("FMA", "tensor cores")[int(rep[14])])
 
@@ -534,7 +535,7 @@ class Solver:
         return dlra_autotune(self.ctx)
 
     def set_stage_kernel(self, variant):
-        """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA."""
+        """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA, 3 cell pairs (FP32, nx even)."""
         dlra_set_stage_kernel(self.ctx, variant)
 
     def set_stencil_gram_kernel(self, variant):

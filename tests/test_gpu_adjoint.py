@@ -43,10 +43,12 @@ def _case(nx=6, nz=6, N=3, K=1, collision=WL.BOLTZMANN, rank_mode=WL.FIXED, rank
     return cfg, [WATER, BONE], w, g
 
 
-def _gpu_grad(cfg, mats, w, beams, g, interval=16, keep=True):
+def _gpu_grad(cfg, mats, w, beams, g, interval=16, keep=True, stage=None):
     from paper_2508_04484_gb300 import dlra as D
     s = D.Solver(cfg, mats, w, beams)
     s.set_adjoint_store(keep)
+    if stage is not None:
+        s.set_stage_kernel(stage)
     s.enable_adjoint(interval)
     e = s.run()
     dbeta, dw = s.backward(g)
@@ -152,6 +154,21 @@ def test_kept_and_recomputed_forward_steps_agree():
         redo = _gpu_grad(cfg, mats, w, beams, g, interval=interval, keep=False)
         assert rel_l2(kept[1], redo[1]) < 1e-12
         assert rel_l2(kept[2], redo[2]) < 1e-9
+
+
+@pytest.mark.parametrize("stage", [2, 3])
+def test_stage_kernel_variants_give_the_same_gradient(stage):
+    # the transposed streaming stage of the reverse sweep in the brick and cell-pair kernels
+    # fixed rank: the variants differ in the last bit, which must not flip an adaptive rank decision
+    cfg, mats, w, _ = _case(nx=8, nz=8, N=3, K=6, rank_mode=WL.FIXED, rank=8, rank_max=16,
+                            precision=WL.FP32_MIXED, seed=2, t100=0.1)
+    n = cfg["nx"] * cfg["nz"]
+    g = np.sin(np.arange(n) * 0.37) + 1.5
+    e0, b0, w0 = _gpu_grad(cfg, mats, w, ONE_BEAM, g, stage=0)
+    e1, b1, w1 = _gpu_grad(cfg, mats, w, ONE_BEAM, g, stage=stage)
+    assert rel_l2(e1, e0) < 1e-5
+    assert rel_l2(b1, b0) < 1e-4
+    assert rel_l2(w1, w0) < 1e-3
 
 
 def test_beam_weights_and_mixture_replacement():

@@ -144,11 +144,11 @@ def test_heterogeneous_cube_fp32_matches_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("case", ["slab", "cube"])
 def test_stage_kernel_variants_match_oracle(case, variant):
-    # the tcgen05 (3xTF32) and the brick-staged streaming stages against the per-cell stage
-    # and the oracle
+    # the tcgen05 (3xTF32), the brick-staged and the cell-pair streaming stages against the
+    # per-cell stage and the oracle
     if case == "slab":
         cfg, mats, w, beams = _slab(precision=WL.FP32_MIXED)
         mode, kw = OP.FIXED, dict(rank=6)
