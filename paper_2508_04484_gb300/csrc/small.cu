@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace dlra {
@@ -806,6 +808,7 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
                             double drop_tol, T* __restrict__ Wh, BeamDims* dims) {
   extern __shared__ __align__(16) unsigned char raw[];
   T* R = reinterpret_cast<T*>(raw);   // m x qcap
+  T* G = R + (size_t)m * qcap;        // RB x qcap projections W^T R; then the r + q projections of u
   T* U = Wh + (long long)RB * m;      // accepted new directions, written in place
   __shared__ T red[32];
   __shared__ T cn[64];
@@ -827,18 +830,26 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
   for (int c = tid; c < qcap; c += nt) used[c] = 0;
   const T scale2 = block_sum(part, red);
   const T thr = T(drop_tol * drop_tol) * scale2;
-  // two passes of R -= W (W^T R)
+  // two passes of R -= W (W^T R) (classical Gram-Schmidt twice): all r qcap projections at
+  // once over the warps, then one fused update per element
   for (int pass = 0; pass < 2; ++pass) {
-    for (int c = wid; c < qcap; c += nw) {
-      for (int a = 0; a < r; ++a) {
-        T d = 0;
-        for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * R[c * m + i];
-        d = warp_sum(d);
-        for (int i = lane; i < m; i += 32) R[c * m + i] -= d * W[(long long)a * m + i];
-      }
+    __syncthreads();
+    for (int e = wid; e < r * qcap; e += nw) {
+      const int a = e % r, c = e / r;
+      T d = 0;
+      for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * R[c * m + i];
+      d = warp_sum(d);
+      if (lane == 0) G[c * RB + a] = d;
     }
     __syncthreads();
+    for (int e = tid; e < m * qcap; e += nt) {
+      const int i = e % m, c = e / m;
+      T v = R[e];
+      for (int a = 0; a < r; ++a) v -= G[c * RB + a] * W[(long long)a * m + i];
+      R[e] = v;
+    }
   }
+  __syncthreads();
   int q = 0;
   for (int it = 0; it < qcap; ++it) {
     for (int c = wid; c < qcap; c += nw) {
@@ -859,29 +870,31 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
     __syncthreads();
     const int b = s_best;
     if (b < 0) break;
-    // u = R[:, b] re-orthogonalised against W and the accepted directions, normalised
+    // u = R[:, b] re-orthogonalised against W and the accepted directions (one classical
+    // Gram-Schmidt pass over all warps, R being orthogonal to both up to round-off already),
+    // normalised
     T* u = U + q * m;
     for (int i = tid; i < m; i += nt) u[i] = R[b * m + i];
     __syncthreads();
-    if (wid == 0) {
-      for (int a = 0; a < r; ++a) {
-        T d = 0;
-        for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * u[i];
-        d = warp_sum(d);
-        for (int i = lane; i < m; i += 32) u[i] -= d * W[(long long)a * m + i];
-      }
-      for (int a = 0; a < q; ++a) {
-        T d = 0;
-        for (int i = lane; i < m; i += 32) d += U[a * m + i] * u[i];
-        d = warp_sum(d);
-        for (int i = lane; i < m; i += 32) u[i] -= d * U[a * m + i];
-      }
-      T n2 = 0;
-      for (int i = lane; i < m; i += 32) n2 += u[i] * u[i];
-      n2 = warp_sum(n2);
-      T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
-      for (int i = lane; i < m; i += 32) u[i] *= inv;
+    for (int a = wid; a < r + q; a += nw) {
+      const T* v = a < r ? W + (long long)a * m : U + (long long)(a - r) * m;
+      T d = 0;
+      for (int i = lane; i < m; i += 32) d += v[i] * u[i];
+      d = warp_sum(d);
+      if (lane == 0) G[a] = d;
     }
+    __syncthreads();
+    T part2 = 0;
+    for (int i = tid; i < m; i += nt) {
+      T x = u[i];
+      for (int a = 0; a < r; ++a) x -= G[a] * W[(long long)a * m + i];
+      for (int a = 0; a < q; ++a) x -= G[r + a] * U[(long long)a * m + i];
+      u[i] = x;
+      part2 += x * x;
+    }
+    const T n2 = block_sum(part2, red);
+    const T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
+    for (int i = tid; i < m; i += nt) u[i] *= inv;
     __syncthreads();
     // remove u from the remaining columns
     for (int c = wid; c < qcap; c += nw) {
@@ -900,7 +913,8 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
 template <typename T, typename KT>
 void launch_waug(cudaStream_t st, const T* W, int m, int RB, const KT* K, long long ldk, int qcap, double drop_tol,
                  T* Wh, BeamDims* dims) {
-  size_t smem = (size_t)m * qcap * sizeof(T);
+  // R (m x qcap) and the projections (RB x qcap; >= RB + qcap for those of one direction)
+  const size_t smem = ((size_t)m * qcap + (size_t)std::max(RB * qcap, RB + qcap)) * sizeof(T);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(waug_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   waug_kernel<T, KT><<<1, 512, smem, st>>>(W, m, RB, K, ldk, qcap, drop_tol, Wh, dims);
