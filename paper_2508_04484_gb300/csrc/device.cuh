@@ -800,30 +800,39 @@ __global__ void __launch_bounds__(128) apply_kernel(long long rows, const T* __r
 #pragma unroll
   for (int c = 0; c < (F2 ? NM / 2 : 1); ++c) acc2[c] = make_float2(0.f, 0.f);
   const T* a = A + i;
-  T cur = Qa > 0 ? a[0] : T(0);
-  for (int q = 0; q < Qa; ++q) {
-    const T nxt = q + 1 < Qa ? a[(long long)(q + 1) * lda] : T(0);
-    const T* mrow = sM + q * NM;
-    if constexpr (F2) {
-      const float2 c2 = make_float2(cur, cur);
+  // eight columns of the row loaded before they are used (eight loads in flight per thread:
+  // the kernel streams n x Q values and is bound by memory latency otherwise); the sum runs
+  // over q in order
+  constexpr int QB = 8;
+  for (int q0 = 0; q0 < Qa; q0 += QB) {
+    T cv[QB];
 #pragma unroll
-      for (int c = 0; c < NM; c += 4) {
-        const float4 m = *reinterpret_cast<const float4*>(mrow + c);
-        acc2[c / 2] = __ffma2_rn(c2, make_float2(m.x, m.y), acc2[c / 2]);
-        acc2[c / 2 + 1] = __ffma2_rn(c2, make_float2(m.z, m.w), acc2[c / 2 + 1]);
-      }
-    } else {
+    for (int u = 0; u < QB; ++u) cv[u] = q0 + u < Qa ? a[(long long)(q0 + u) * lda] : T(0);
 #pragma unroll
-      for (int c = 0; c < NM; c += 4) {
-        T m4[4];
-        Vec4<T>::load(mrow + c, m4);
-        acc[c] += cur * m4[0];
-        acc[c + 1] += cur * m4[1];
-        acc[c + 2] += cur * m4[2];
-        acc[c + 3] += cur * m4[3];
+    for (int u = 0; u < QB; ++u) {
+      if (q0 + u >= Qa) break;
+      const T cur = cv[u];
+      const T* mrow = sM + (q0 + u) * NM;
+      if constexpr (F2) {
+        const float2 c2 = make_float2(cur, cur);
+#pragma unroll
+        for (int c = 0; c < NM; c += 4) {
+          const float4 m = *reinterpret_cast<const float4*>(mrow + c);
+          acc2[c / 2] = __ffma2_rn(c2, make_float2(m.x, m.y), acc2[c / 2]);
+          acc2[c / 2 + 1] = __ffma2_rn(c2, make_float2(m.z, m.w), acc2[c / 2 + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NM; c += 4) {
+          T m4[4];
+          Vec4<T>::load(mrow + c, m4);
+          acc[c] += cur * m4[0];
+          acc[c + 1] += cur * m4[1];
+          acc[c + 2] += cur * m4[2];
+          acc[c + 3] += cur * m4[3];
+        }
       }
     }
-    cur = nxt;
   }
   if constexpr (F2) {
 #pragma unroll
