@@ -1769,7 +1769,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   // the streaming stage reads most of its inputs from DRAM inside a solve (the other chains of
   // the step evict them from L2): its variants are timed one launch at a time after a write of
-  // 256 MB, which a warm loop of launches would misjudge
+  // 256 MB (a warm loop of launches gets their order wrong)
   const size_t flush_bytes = (size_t)256 << 20;
   void* flush = nullptr;
   CK(cudaMalloc(&flush, flush_bytes));
