@@ -49,7 +49,7 @@ typedef enum {
 
 enum { DLRA_FOKKER_PLANCK = 0, DLRA_BOLTZMANN = 1 };
 enum { DLRA_RANK_FIXED = 0, DLRA_RANK_ADAPTIVE = 1, DLRA_RANK_SCHEDULE = 2 };
-enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1 };
+enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1, DLRA_FP32_SPLIT = 2 };
 
 /* Problem configuration (Sec. 3.3, Sec. 4).
  *  nx, ny, nz, dx, dy, dz : voxel grid, cell index (k*ny + j)*nx + i (Sec. 3.3.2).
@@ -70,7 +70,9 @@ enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1 };
  *  cfl_max                : streaming RK4 sub-steps per energy step are
  *                           ceil(dE sum_d lam_max/delta_d / (min_x S(x,E_k) cfl_max)).
  *  precision              : DLRA_FP64, or DLRA_FP32_MIXED (FP32 n-side data and
- *                           arithmetic, FP64 reductions, factorisations and S).
+ *                           arithmetic, FP64 reductions, factorisations and S), or
+ *                           DLRA_FP32_SPLIT (as DLRA_FP32_MIXED with the 2r x 2r
+ *                           truncation SVD and the Galerkin S-step in FP64 arithmetic).
  *  bk_p, bk_alpha         : Bragg-Kleeman water stopping power S_w(E) = E^(1-p)/(p alpha).
  *  t100                   : water scattering power at 100 MeV, T_w(E) = t100 (100/E)^2.
  *  max_concurrent_beams   : beams advanced concurrently (one work space and stream pair

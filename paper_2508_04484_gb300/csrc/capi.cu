@@ -476,6 +476,7 @@ struct dlra_ctx {
   dlra_status poisoned = DLRA_OK;
   cudaStream_t st = nullptr;
   bool fp64 = true;
+  bool small64 = true;  // truncation SVD and Galerkin S-step in FP64 (FP64 and FP32-split paths)
   int n = 0, m = 0, N = 0, K = 0, M = 0, RB = 0, nk = 0, n2 = 0;
   bool two_d = false;
   Geo geo{};
@@ -697,6 +698,16 @@ struct Engine {
     rp.schedule = adj_rank ? nullptr : ctx->schedule_dev;
     return rp;
   }
+  // truncation SVD of S^ (n2 x n2, FP64 in memory), in FP64 arithmetic where small64 is set;
+  // the rank tolerances stay those of the n-side precision, which sets the noise floor of S^
+  void svd_truncate(double* Sh, int n2, int RB, int k, int event, Beam<T>& B) {
+    if (ctx->small64)
+      launch_svd_truncate<double>(L->s0, Sh, n2, RB, rank_params(), k, event, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
+                                  ctx->dev_err);
+    else
+      launch_svd_truncate<T>(L->s0, Sh, n2, RB, rank_params(), k, event, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
+                             ctx->dev_err);
+  }
   double drop1() const { return sizeof(T) == 8 ? 1e-12 : 3e-4; }
   double drop2() const { return sizeof(T) == 8 ? 1e-8 : 1e-3; }
 
@@ -855,10 +866,13 @@ struct Engine {
     cudaMemsetAsync(L->Ph, 0, sizeof(double) * nk * n2 * n2, sm);
     gram<T>(sm, m, Wh, m, nullptr, n2, nk * n2, FPlain<T>{Zm, m, nullptr, nk * n2}, L->Ph, n2, nl);
     join();
-    launch_sstep<T>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, L->Sh);
+    if (ctx->small64)
+      launch_sstep<double>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns,
+                           L->Sh);
+    else
+      launch_sstep<T>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, L->Sh);
     ++nl;
-    launch_svd_truncate<T>(st, L->Sh, n2, RB, rank_params(), k, 0, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
-                           ctx->dev_err);
+    svd_truncate(L->Sh, n2, RB, k, 0, B);
     ++nl;
     apply_truncation(B);
   }
@@ -904,8 +918,7 @@ struct Engine {
     join();
     launch_src_assemble<T>(st, B.S, RB, L->XA, Bk, P(L->Wh), m, Ms, n2, ctx->h, L->Sh);
     ++nl;
-    launch_svd_truncate<T>(st, L->Sh, n2, RB, rank_params(), k, 1, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
-                           ctx->dev_err);
+    svd_truncate(L->Sh, n2, RB, k, 1, B);
     ++nl;
     apply_truncation(B);
   }
@@ -2001,7 +2014,8 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
   if (g.sh_degree < 1 || g.sh_degree > 31) return fail(ctx, DLRA_ERR_ARG, "sh_degree must be in [1, 31]");
   if (g.collision != DLRA_FOKKER_PLANCK && g.collision != DLRA_BOLTZMANN) return fail(ctx, DLRA_ERR_ARG, "bad collision");
   if (g.rank_mode < 0 || g.rank_mode > 2) return fail(ctx, DLRA_ERR_ARG, "bad rank_mode");
-  if (g.precision != DLRA_FP64 && g.precision != DLRA_FP32_MIXED) return fail(ctx, DLRA_ERR_ARG, "bad precision");
+  if (g.precision != DLRA_FP64 && g.precision != DLRA_FP32_MIXED && g.precision != DLRA_FP32_SPLIT)
+    return fail(ctx, DLRA_ERR_ARG, "bad precision");
   if (g.rank_max < 1 || g.rank_max > 64) return fail(ctx, DLRA_ERR_ARG, "rank_max must be in [1, 64]");
   if (g.rank_mode == DLRA_RANK_FIXED && (g.rank < 1 || g.rank > g.rank_max))
     return fail(ctx, DLRA_ERR_ARG, "rank must be in [1, rank_max]");
@@ -2012,6 +2026,7 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
   if (!(g.bk_p > 1 && g.bk_p < 2 && g.bk_alpha > 0 && g.t100 >= 0))
     return fail(ctx, DLRA_ERR_ARG, "need 1 < bk_p < 2, bk_alpha > 0, t100 >= 0");
   ctx->fp64 = g.precision == DLRA_FP64;
+  ctx->small64 = g.precision != DLRA_FP32_MIXED;
   if (g.max_concurrent_beams < 0) return fail(ctx, DLRA_ERR_ARG, "max_concurrent_beams must be >= 0");
   ctx->max_lanes = g.max_concurrent_beams > 0 ? g.max_concurrent_beams : 8;
   if (ctx->fp64 && g.rank_max > 32) return fail(ctx, DLRA_ERR_ARG, "FP64 precision supports rank_max <= 32");

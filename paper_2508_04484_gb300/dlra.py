@@ -23,7 +23,7 @@ STATUS = {0: "DLRA_OK", 1: "DLRA_ERR_ARG", 2: "DLRA_ERR_STATE", 3: "DLRA_ERR_CUD
           5: "DLRA_ERR_NONFINITE", 6: "DLRA_ERR_RANK", 7: "DLRA_ERR_TIMEOUT"}
 FOKKER_PLANCK, BOLTZMANN = 0, 1
 RANK_FIXED, RANK_ADAPTIVE, RANK_SCHEDULE = 0, 1, 2
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP32_SPLIT = 0, 1, 2
 
 
 class DlraError(RuntimeError):

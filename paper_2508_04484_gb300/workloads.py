@@ -22,7 +22,7 @@ import numpy as np
 
 FP, BOLTZMANN = 0, 1
 FIXED, ADAPTIVE, SCHEDULE = 0, 1, 2
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP32_SPLIT = 0, 1, 2
 
 WATER = dict(density=1.0, sp_ratio=1.0, scatter_ratio=1.0, screening=1.0e-3)
 BONE = dict(density=1.85, sp_ratio=0.90, scatter_ratio=1.35, screening=1.5e-3)

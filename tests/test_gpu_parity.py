@@ -104,7 +104,7 @@ def test_one_energy_step_from_a_state(precision, tol):
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(WL.FP64, 1e-5), (WL.FP32_MIXED, 1e-3)])
+@pytest.mark.parametrize("precision,tol", [(WL.FP64, 1e-5), (WL.FP32_MIXED, 1e-3), (WL.FP32_SPLIT, 1e-3)])
 def test_slab_run_matches_oracle(precision, tol):
     cfg, mats, w, beams = _slab(precision=precision)
     prob = oracle_problem(cfg, mats, w)
@@ -133,13 +133,16 @@ def test_rewound_solve_matches_oracle(precision, tol):
     s.close()
 
 
-def test_heterogeneous_cube_fp32_matches_oracle():
+@pytest.mark.parametrize("precision", [WL.FP32_MIXED, WL.FP32_SPLIT])
+def test_heterogeneous_cube_fp32_matches_oracle(precision):
+    # FP32 stencil and contractions; the truncation SVD and S-step in FP32 (mixed) or FP64 (split)
     cfg, mats, w, beams = _cube()
     prob = oracle_problem(cfg, mats, w)
     src = oracle_sources(prob, beams)
     dose, res = oracle_dlra(prob, src, OP.ADAPTIVE, tol=1e-3, r_max=12)
-    s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"])
+    s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=precision)
     dg = s.run()
+    print("precision", precision, "dose error against the FP64 oracle", rel_l2(dg, dose))
     assert rel_l2(dg, dose) < 1e-3
     s.close()
 
