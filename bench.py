@@ -341,6 +341,16 @@ def main():
     log = solver.rank_log(0)[:K]
     nsub = nsub[:K]
     r_start, updates, stage_launches = _rank_stats(log, nsub, n)
+    # the ray trace alone (part of every timed solve): reset with a fresh trace, best of three
+    # (after the rank log of the warm-up solve is read: a reset clears it; every timed solve
+    # starts with the same reset)
+    rt_ms = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        solver.reset(retrace=True)
+        torch.cuda.synchronize()
+        rt_ms.append((time.perf_counter() - t0) * 1000.0)
+    raytrace_ms = min(rt_ms)
     clocks = Clocks(dev.index)
     # ---- timed region: K whole solves, L2 flushed between them ----
     if ws > 1:
@@ -403,6 +413,8 @@ def main():
     if variant == 3 and cfg["nx"] % 2:
         variant = 0
     traffic, traffic_note = _stage_traffic(variant)
+    # the same launch measured by its DRAM bytes (ncu capture) over its CUDA-event time
+    traffic_gbs = traffic / (avg_launch_ms / 1000.0) / 1e9 if traffic else None
     kname = f"{STAGE_KERNELS[variant][0]} (fused RK4 streaming stage: stencil + r x r mix)"
     if frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
@@ -410,12 +422,14 @@ def main():
                 "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
                 "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
-                "achieved_gbs": gbs, "hbm_frac": frac_hbm, "avg_launch_us": avg_launch_ms * 1000.0}
+                "achieved_gbs": gbs, "hbm_frac": frac_hbm, "avg_launch_us": avg_launch_ms * 1000.0,
+                "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
                 "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
                 "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
                 "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "alu_frac": frac_alu,
+                "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
                 "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
                 "avg_launch_us": avg_launch_ms * 1000.0}
     # ---- end to end through the public API with host buffers ----
@@ -482,7 +496,9 @@ def main():
                 "energy_steps_per_s": value,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs, "autotune": tuned}
+                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs, "autotune": tuned,
+                "raytrace_ms": {"value": raytrace_ms, "timing": "host wall clock around a reset with a fresh "
+                                "ray trace of every beam and a synchronise, best of three; included in each step"}}
         if args.workload != WORKLOAD:
             line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
                               "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,
