@@ -19,6 +19,9 @@ Modules (each function cites the part of the paper it follows):
 * ``dlra``     -- the augmented-BUG low-rank energy step (Sec. 2.2, Sec. 3.3.3).
 * ``adjoint``  -- discrete adjoint of the full-rank solve: gradients of a loss of the
                   deposited energy with respect to beam and mixture weights.
+* ``straggling`` -- uncollided energy distribution along a ray with straggling: energy
+                  DG (P2, Lax-Friedrichs slowing down, SIPG straggling), Crank-Nicolson in
+                  depth (Sec. 3.2); the GPU path does not have it yet.
 
 Parity status of each function is stated in its module header; where a
 function has no independent pin it says "parity unpinned".
