@@ -9,7 +9,9 @@ mathematics fixes, independent of the scheme's own formulas:
 * the Bohr straggling rate of water against the tabulated constant 0.157 MeV^2 cm^2/g x Z/A;
 * absorption alone is the Crank-Nicolson amplification factor, and exp(-Sigma z) to O(h^2);
 * without straggling the mean energy follows the CSDA range-energy relation and the energy
-  lost to slowing down equals the drop of the integrated energy.
+  lost to slowing down equals the drop of the integrated energy;
+* whole beams: without straggling the DG tracer converges to the independent CSDA tracer of
+  oracle/raytrace.py; particle and energy balances close to round-off with straggling.
 """
 import numpy as np
 import pytest
@@ -130,3 +132,75 @@ def test_sipg_operator_is_symmetric_positive_semidefinite():
     # constants are in its kernel (no flux through the ends, no jumps)
     one = dg.project(lambda E: 1.0 + 0.0 * E)
     assert np.abs(K @ one).max() < 1e-12
+
+
+def _slab_problem(e_max=66.0):
+    from oracle import problem as OP
+    from paper_2508_04484_gb300 import workloads as WL
+    cfg = WL.base_config(nx=16, ny=1, nz=20, dx=0.2, dy=0.0, dz=0.2, N=3, collision=WL.BOLTZMANN,
+                         rank_mode=WL.FIXED, rank=4, rank_max=8, e_max=e_max, e_min=30.0, n_steps=8,
+                         precision=WL.FP64, t100=2e-2)
+    mats, w = WL.homogeneous(cfg)
+    return OP.Problem(cfg, mats, w)
+
+
+def _pencil(**kw):
+    from paper_2508_04484_gb300 import workloads as WL
+    return WL.pencil_beam(60.0, (1.3, 0.0, 0.0), (0.2, 0.0, 1.0), **kw)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_without_straggling_the_dg_tracer_converges_to_the_csda_tracer():
+    # two independent discretisations of the same CSDA ray (closed-form range-energy segments with
+    # nested quadrature, against the energy-DG march): their deposits and fluences converge to each
+    # other, and the energy carried into the collided flux agrees to round-off level
+    from oracle import raytrace as ORT
+    prob = _slab_problem()
+    beam = _pencil(spot_sigma=0.0)
+    ref = ORT.trace(prob, beam)
+    coarse = ST.trace_straggling(prob, beam, n_elem=128, h_max=0.01, straggling=False)
+    fine = ST.trace_straggling(prob, beam, n_elem=256, h_max=0.005, straggling=False)
+    assert _rel(coarse.e_u, ref.e_u) < 2e-2 and _rel(fine.e_u, ref.e_u) < 2e-3
+    assert _rel(coarse.psi.sum(0), ref.psi.sum(0)) < 1.5e-2 and _rel(fine.psi.sum(0), ref.psi.sum(0)) < 1e-3
+    assert _rel(fine.psi, ref.psi) < 1.5e-2
+    for r in (coarse, fine):
+        assert abs(r.removed_energy / ref.removed_energy - 1.0) < 1e-7
+        assert abs(r.cutoff_energy / ref.cutoff_energy - 1.0) < 1e-7
+
+
+@pytest.mark.parametrize("e_max", [60.0, 66.0])
+@pytest.mark.parametrize("straggling", [False, True])
+def test_tracer_balances_are_exact(e_max, straggling):
+    # particles: in = exit + removed + below E_min; energy: in = deposit + removed + exit +
+    # E_min x (below E_min) + the no-flux ends' term, to round-off
+    prob = _slab_problem(e_max)
+    r = ST.trace_straggling(prob, _pencil(spot_sigma=0.1), straggling=straggling)
+    V = prob.volume
+    n_in = 1.0   # unit beam weight
+    assert abs(n_in - (r.removed_particles + r.cutoff_particles + r.exit_particles)) < 1e-12
+    e_out = r.e_u.sum() * V + r.removed_energy + r.exit_energy + r.cutoff_energy + r.boundary_energy
+    assert abs(r.input_energy - e_out) < 1e-12 * r.input_energy
+    # the ends' term is a boundary effect of the scheme: small against the beam's energy
+    assert abs(r.boundary_energy) < 1e-4 * r.input_energy
+    if not straggling:
+        assert r.boundary_energy == 0.0
+
+
+def test_straggling_spreads_the_energy_distribution_of_a_beam():
+    # a 100 MeV beam through 5 cm of water: its energy variance grows by about int T dz
+    # (Bohr, plus the growth a falling energy gives an existing spread)
+    dg = ST.EnergyDG(20.0, 110.0, 128)
+    Sw = lambda E: E ** (1.0 - 1.77) / (1.77 * 0.0022)
+    plain = ST.RayMarch(dg, Sw, _const(0.0))
+    strag = ST.RayMarch(dg, Sw, ST.straggling_water)
+    c0 = dg.project(_gauss(100.0, 0.5))
+    c_p, _ = plain.march(c0, [(5.0, 1.0, 0.0)])
+    c_s, _ = strag.march(c0, [(5.0, 1.0, 0.0)])
+    (m_p, v_p), (m_s, v_s) = dg.mean_var(c_p), dg.mean_var(c_s)
+    added = v_s - v_p
+    bohr = ST.t_bohr_water() * 5.0
+    assert abs(m_s - m_p) < 1e-2
+    assert 1.0 * bohr < added < 2.5 * bohr
