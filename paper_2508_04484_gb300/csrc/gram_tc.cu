@@ -3,13 +3,16 @@
 //   G_k[a][b] = sum_i A(i, a) D_k(rho^-1 B(:, b))(i),   k = 2 da + s,
 // written as D[j][a] = sum_t S[j][t] A[t][a] with j = k nb + b and the cells t as the
 // contraction index. A CTA owns a slice of up to 256 rows j (two 128-row MMA tiles, TMEM
-// lanes = j, TMEM columns = a) and walks 32-cell chunks of the grid: it forms the stencil
-// values S of the chunk (13 neighbour loads per column and cell, as in the FMA kernel), splits
-// them and the chunk's A rows into TF32 high and low parts, stores both K-major in shared
-// memory and issues three tcgen05.mma kind::tf32 per 8-cell K-slice (hi*hi + hi*lo + lo*hi,
-// FP32-accurate products, FP32 accumulation in tensor memory). Two operand buffers: the next
-// chunk is staged while the tensor core reads the current one. The slice's partial sums are
-// added to the FP64 output with one atomic per entry at the end.
+// lanes = j, TMEM columns = a) and walks a contiguous run of 32-cell chunks of the grid: its
+// warps form the stencil values S of the chunk (where nx % 4 == 0 a lane takes four
+// x-consecutive cells of one column from eleven float4 loads of the column and of rho^-1;
+// otherwise one cell per lane from per-lane neighbour tables), split them and the chunk's A
+// rows into TF32 high and low parts and store both K-major in shared memory; one thread (of
+// the last warp, which forms no stencil values on the float4 path) issues three
+// tcgen05.mma kind::tf32 per 8-cell K-slice (hi*hi + hi*lo + lo*hi, FP32-accurate products,
+// FP32 accumulation in tensor memory). Two operand buffers: the next chunk is staged while the
+// tensor core reads the current one. The slice's partial sums are added to the FP64 output
+// with one atomic per entry at the end.
 #include <cuda_runtime.h>
 
 #include <algorithm>
