@@ -345,6 +345,32 @@ typedef struct {
  * incomplete); errors read with dlra_last_error(NULL). */
 dlra_status dlra_stencil_gram(const dlra_stencil_gram_args* args);
 
+/* Arguments of the straggling tables (host only, no context, no device memory). */
+typedef struct {
+  double e_min, e_max;    /* energy interval of the discretisation, MeV (0 < e_min < e_max) */
+  int32_t n_elem;         /* equal energy elements (the paper uses 128), 1 .. 65536 */
+  double bk_p, bk_alpha;  /* water stopping power S_w(E) = E^(1-p) / (p alpha) */
+  double t100;            /* removal reference Sigma_t / tau = t100 (100 / E)^2 / 2 */
+  int32_t straggling;     /* 0: T = 0 (the CSDA limit) */
+} dlra_straggling_args;
+
+/* The operators of the uncollided transport along a ray with energy straggling (Sec. 3.2:
+ * d psi/dz + Sigma_t psi = d(S* psi)/dE + (1/2) d/dE (T d psi/dE), S* = S + T'/2), discretised
+ * in energy by discontinuous Galerkin with the Legendre polynomials P_0..P_2 of each element, a
+ * Lax-Friedrichs flux for slowing down and SIPG for straggling (penalty 18 kappa / Delta, no
+ * diffusive flux through the ends), for water (S_w above; T_w = T_Bohr (1 + 4 I/(3 m_e v^2)
+ * ln(2 m_e v^2 / I)), I = 75 eV) and a unit material factor. Host outputs, caller-allocated:
+ *   mass [3 n_elem]           diagonal of the mass matrix (Delta / (2 j + 1));
+ *   adv, sipg, rem [n_elem][3][3][3]  block-tridiagonal operators: block (e, b) couples the
+ *     dofs i of element e (rows) with the dofs j of element e - 1 + b (b = 0, 1, 2; blocks
+ *     outside the interval are zero); adv is the slowing-down term int d(S* psi)/dE v,
+ *     sipg the SIPG form of kappa = T/2, rem the removal int sigma_ref psi v.
+ * A ray segment with stopping factor f and removal factor tau advances by
+ * M dc/dz = -(-f adv + f sipg + tau rem) c. Errors: DLRA_ERR_ARG (read with
+ * dlra_last_error(NULL)). */
+dlra_status dlra_straggling_tables(const dlra_straggling_args* args, double* mass, double* adv, double* sipg,
+                                   double* rem);
+
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);
 

@@ -72,6 +72,12 @@ class dlra_stencil_gram_args(C.Structure):
                 ("cuda_stream", C.c_void_p)]
 
 
+class dlra_straggling_args(C.Structure):
+    _fields_ = [("e_min", C.c_double), ("e_max", C.c_double), ("n_elem", C.c_int32),
+                ("bk_p", C.c_double), ("bk_alpha", C.c_double), ("t100", C.c_double),
+                ("straggling", C.c_int32)]
+
+
 # names, argument types and return type of every entry point of include/dlra.h
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -104,6 +110,7 @@ SIGNATURES = {
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_stencil_gram": ([C.POINTER(dlra_stencil_gram_args)], C.c_int),
+    "dlra_straggling_tables": ([C.POINTER(dlra_straggling_args), _DP, _DP, _DP, _DP], C.c_int),
     "dlra_launch_count": ([_P], C.c_int64),
     "dlra_last_error": ([_P], C.c_char_p),
     "dlra_destroy": ([_P], None),
@@ -429,6 +436,21 @@ def stencil_gram(grid, spacing, A, B, inv_rho, variant=0):
                                   torch.cuda.current_stream(A.device).cuda_stream)
     dlra_stencil_gram(args)
     return out
+
+
+def straggling_tables(e_min, e_max, n_elem=128, bk_p=1.77, bk_alpha=0.0022, t100=1.72e-4, straggling=True):
+    """Host tables of the straggling ray model (dlra_straggling_tables): mass (3 G,) and the
+    block-tridiagonal adv, sipg, rem (G, 3, 3, 3) for G = n_elem energy elements."""
+    a = dlra_straggling_args(float(e_min), float(e_max), int(n_elem), float(bk_p), float(bk_alpha), float(t100),
+                             int(bool(straggling)))
+    mass = np.zeros(3 * n_elem)
+    adv = np.zeros((n_elem, 3, 3, 3))
+    sipg = np.zeros((n_elem, 3, 3, 3))
+    rem = np.zeros((n_elem, 3, 3, 3))
+    st = load().dlra_straggling_tables(C.byref(a), _dptr(mass), _dptr(adv), _dptr(sipg), _dptr(rem))
+    if st != DLRA_OK:
+        raise DlraError(st, load().dlra_last_error(None).decode())
+    return mass, adv, sipg, rem
 
 
 def dlra_launch_count(ctx) -> int:
