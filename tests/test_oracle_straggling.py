@@ -204,3 +204,23 @@ def test_straggling_spreads_the_energy_distribution_of_a_beam():
     bohr = ST.t_bohr_water() * 5.0
     assert abs(m_s - m_p) < 1e-2
     assert 1.0 * bohr < added < 2.5 * bohr
+
+
+def test_collided_dose_from_the_dg_source_converges_to_the_csda_one():
+    # the whole oracle path with the straggling tracer as the source (straggling off): the
+    # low-rank collided solve and its dose converge to those driven by the CSDA tracer
+    from oracle import dlra as ODL
+    from oracle import problem as OP
+    from oracle import raytrace as ORT
+    prob = _slab_problem()
+    beam = _pencil(spot_sigma=0.0)
+    d = np.asarray(beam["dir"]) / np.linalg.norm(beam["dir"])
+    ref = ORT.trace(prob, beam)
+    r_ref = ODL.solve(prob, [(ref.psi, ref.e_u, d)], ODL.RankControl(mode=OP.FIXED, rank=6))
+    errs = []
+    for G, h in ((128, 0.01), (256, 0.005)):
+        r = ST.trace_straggling(prob, beam, n_elem=G, h_max=h, straggling=False)
+        out = ODL.solve(prob, [(r.psi, r.e_u, d)], ODL.RankControl(mode=OP.FIXED, rank=6))
+        errs.append((_rel(out["dose"], r_ref["dose"]), _rel(out["dose_collided"], r_ref["dose_collided"])))
+    assert errs[0][0] < 2e-2 and errs[1][0] < 1e-3
+    assert errs[0][1] < 2e-2 and errs[1][1] < 2e-3
