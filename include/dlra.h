@@ -371,6 +371,44 @@ typedef struct {
 dlra_status dlra_straggling_tables(const dlra_straggling_args* args, double* mass, double* adv, double* sipg,
                                    double* rem);
 
+/* Arguments of the stand-alone straggling ray trace (no context). Device memory of the current
+ * device, ordered with cuda_stream:
+ *   f_cell [n]  stopping factor rho_s(x) (S(x, E) = f S_w(E)); T(x, E) = f T_w(E);
+ *   tau_cell [n] removal factor (Sigma_t(x, E) = tau t100 (100/E)^2 / 2, the ray tracer's model);
+ *   psi [n_bins][n] (out) bin-averaged uncollided fluence of a unit-weight beam per energy bin
+ *     [E_{k+1}, E_k], E_k = e_max - k (e_max - e_min) / n_bins, and voxel (1/(cm^2 MeV));
+ *   e_u [n] (out) energy lost to slowing down per volume (MeV/cm^3).
+ * Grid as for dlra_kstep_args; the energy interval is discretised by n_elem DG elements (the
+ * paper: 128) and the depth by Crank-Nicolson steps of at most h_max cm (the paper: 0.01);
+ * straggling = 0 gives the CSDA limit. Beam: spot grid of pitch min(delta)/4 within 3.5
+ * spot_sigma with Gaussian weights, initial energy distribution a Gaussian of energy_sigma
+ * (a delta for 0) projected on the DG space. n_elem >= 1 with at most 8 energy bins
+ * overlapping one element. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  double e_min, e_max;
+  int32_t n_bins, n_elem;
+  double h_max;
+  double bk_p, bk_alpha, t100;
+  int32_t straggling;
+  double energy, energy_sigma, spot_sigma;
+  double pos[3], dir[3];
+  const double* f_cell;
+  const double* tau_cell;
+  double* psi;
+  double* e_u;
+  void* cuda_stream;
+} dlra_straggling_trace_args;
+
+/* The uncollided transport of one beam with energy straggling (Sec. 3.2: energy DG with a
+ * Lax-Friedrichs slowing-down flux and SIPG straggling, Crank-Nicolson in depth), one device
+ * thread per ray marching the block-tridiagonal system with FP64 Thomas elimination.
+ * Overwrites psi and e_u; allocates its tables and work space (3 G x 4 + 18 G doubles per ray)
+ * and frees them; synchronises cuda_stream. Errors: DLRA_ERR_ARG, DLRA_ERR_OOM, DLRA_ERR_CUDA
+ * (dlra_last_error(NULL)). Not yet run on a GB300 (its tests are skipped). */
+dlra_status dlra_straggling_trace(const dlra_straggling_trace_args* args);
+
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);
 

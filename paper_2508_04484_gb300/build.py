@@ -19,9 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "small.cu", "raytrace.cu", "adjoint.cu", "gram_tc.cu", "noalloc.cu", "tables.cpp",
-           "straggling_tables.cpp"]
-HEADERS = ["device.cuh", "kernels.h", "tables.h", "tcgen05.cuh", "kstage_tc.cuh"]
+SOURCES = ["capi.cu", "small.cu", "raytrace.cu", "adjoint.cu", "gram_tc.cu", "noalloc.cu", "straggling.cu",
+           "tables.cpp", "straggling_tables.cpp"]
+HEADERS = ["device.cuh", "kernels.h", "tables.h", "tcgen05.cuh", "kstage_tc.cuh", "straggling_march.cuh"]
 
 
 def _nvcc():

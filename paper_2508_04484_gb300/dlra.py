@@ -78,6 +78,17 @@ class dlra_straggling_args(C.Structure):
                 ("straggling", C.c_int32)]
 
 
+class dlra_straggling_trace_args(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("e_min", C.c_double), ("e_max", C.c_double), ("n_bins", C.c_int32), ("n_elem", C.c_int32),
+                ("h_max", C.c_double), ("bk_p", C.c_double), ("bk_alpha", C.c_double), ("t100", C.c_double),
+                ("straggling", C.c_int32), ("energy", C.c_double), ("energy_sigma", C.c_double),
+                ("spot_sigma", C.c_double), ("pos", C.c_double * 3), ("dir", C.c_double * 3),
+                ("f_cell", C.c_void_p), ("tau_cell", C.c_void_p), ("psi", C.c_void_p), ("e_u", C.c_void_p),
+                ("cuda_stream", C.c_void_p)]
+
+
 # names, argument types and return type of every entry point of include/dlra.h
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -111,6 +122,7 @@ SIGNATURES = {
     "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_stencil_gram": ([C.POINTER(dlra_stencil_gram_args)], C.c_int),
     "dlra_straggling_tables": ([C.POINTER(dlra_straggling_args), _DP, _DP, _DP, _DP], C.c_int),
+    "dlra_straggling_trace": ([C.POINTER(dlra_straggling_trace_args)], C.c_int),
     "dlra_launch_count": ([_P], C.c_int64),
     "dlra_last_error": ([_P], C.c_char_p),
     "dlra_destroy": ([_P], None),
@@ -451,6 +463,29 @@ def straggling_tables(e_min, e_max, n_elem=128, bk_p=1.77, bk_alpha=0.0022, t100
     if st != DLRA_OK:
         raise DlraError(st, load().dlra_last_error(None).decode())
     return mass, adv, sipg, rem
+
+
+def straggling_trace(cfg, beam, f_cell, tau_cell, n_elem=128, h_max=0.01, straggling=True, stream=None):
+    """Uncollided fluence and deposit of one unit-weight beam with energy straggling
+    (dlra_straggling_trace) on the grid and energy bins of cfg. f_cell, tau_cell: FP64 device
+    tensors (n,), the stopping and removal factors. Returns FP64 device tensors psi (K, n), e_u (n)."""
+    import torch
+    dev = f_cell.device
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    K = cfg["n_steps"]
+    psi = torch.empty((K, n), dtype=torch.float64, device=dev)
+    e_u = torch.empty(n, dtype=torch.float64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    a = dlra_straggling_trace_args(
+        cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["e_min"], cfg["e_max"], K,
+        int(n_elem), float(h_max), cfg["bk_p"], cfg["bk_alpha"], cfg["t100"], int(bool(straggling)),
+        float(beam["energy"]), float(beam.get("energy_sigma", 0.0)), float(beam.get("spot_sigma", 0.0)),
+        (C.c_double * 3)(*beam["pos"]), (C.c_double * 3)(*beam["dir"]),
+        f_cell.data_ptr(), tau_cell.data_ptr(), psi.data_ptr(), e_u.data_ptr(), st)
+    code = load().dlra_straggling_trace(C.byref(a))
+    if code != DLRA_OK:
+        raise DlraError(code, load().dlra_last_error(None).decode())
+    return psi, e_u
 
 
 def dlra_launch_count(ctx) -> int:

@@ -72,3 +72,15 @@ def test_a_march_on_the_library_tables_keeps_the_exact_moments(D):
     assert abs(dg.number(c) / n0 - 1.0) < 1e-12
     m, v = dg.mean_var(c)
     assert m < 100.0 and v > 1.5 ** 2
+
+
+def test_straggling_trace_rejects_bad_arguments_on_the_host(D):
+    # argument checks run before any CUDA call
+    import ctypes as C
+    a = D.dlra_straggling_trace_args()
+    a.nx = a.ny = a.nz = 4
+    a.dx = a.dy = a.dz = 0.1
+    a.e_min, a.e_max, a.n_bins, a.n_elem, a.h_max = 30.0, 60.0, 8, 16, 0.01
+    a.bk_p, a.bk_alpha, a.t100, a.energy = 1.77, 0.0022, 1e-2, 70.0   # energy above e_max
+    assert D.load().dlra_straggling_trace(C.byref(a)) == 1
+    assert b"arguments" in D.load().dlra_last_error(None)
