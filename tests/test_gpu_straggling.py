@@ -2,7 +2,8 @@
 energy-DG tracer (oracle/straggling.py trace_straggling): the same discretisation (128 P2 energy
 elements, Lax-Friedrichs slowing down, SIPG straggling, Crank-Nicolson steps <= 0.01 cm), so the
 bin-averaged fluence and the deposit agree to FP64 round-off. A host build of the same
-preparation and per-ray march matched the oracle to 3e-15 on these cases."""
+preparation and per-ray march matches the oracle to 3e-15 on these cases
+(tests/test_straggling_host_march.py)."""
 import numpy as np
 import pytest
 
