@@ -142,3 +142,31 @@ def test_schedule_replay_reproduces_run():
     b = DL.solve(prob, src, DL.RankControl(mode=P.SCHEDULE, schedule=a["ranks"]))
     assert np.array_equal(a["ranks"], b["ranks"])
     assert np.abs(a["dose"] - b["dose"]).max() == 0.0
+
+
+@pytest.mark.parametrize("density", [1.0, 1.85])
+def test_pure_scattering_has_the_closed_form(density):
+    # Fokker-Planck in a homogeneous medium: the implicit collided step acts on every moment p
+    # alone, u_p <- u_p / (1 + h xi_1 l(l+1) / (2 S)) at E_{k+1} with S = rho S_w(E) (Bragg-Kleeman)
+    # and xi_1 = rho T_w(E) / 2, T_w = t100 (100/E)^2. The full-rank factor is that closed form,
+    # and the low-rank L-step keeps the column space of X, so it reproduces it exactly for any
+    # rank (Sec. 3.3.3 step 1)
+    prob = _problem(6, 5, 4, "fp", n_steps=3, e_max=60.0, e_min=54.0, mats=[dict(density=density)])
+    k = 1
+    E1 = prob.E[k + 1]
+    p, alpha, t100 = 1.77, 0.0022, 1e-2
+    S = density * E1 ** (1.0 - p) / (p * alpha)
+    xi1 = density * t100 * (100.0 / E1) ** 2 / 2.0
+    ell = np.array([int(math.isqrt(q)) for q in range(prob.m)])
+    closed = 1.0 / (1.0 + prob.h * xi1 * ell * (ell + 1) / (2.0 * S))
+    f = FR.scatter_factor(prob, k)
+    assert np.allclose(1.0 / (1.0 - f), closed[None, :], rtol=1e-13, atol=0.0)
+    rng = np.random.default_rng(4)
+    for r in (1, 3, 7):
+        X, _ = np.linalg.qr(rng.standard_normal((prob.n, r)))
+        W, _ = np.linalg.qr(rng.standard_normal((prob.m, r)))
+        S0 = rng.standard_normal((r, r))
+        X1, S1, W1 = DL.collided_scatter(prob, X, S0, W, k)
+        u0 = X @ S0 @ W.T
+        u1 = X1 @ S1 @ W1.T
+        assert np.linalg.norm(u1 - u0 * closed[None, :]) < 1e-13 * np.linalg.norm(u0)
