@@ -28,6 +28,10 @@ namespace {
 using strag::kMaxBinsPerElem;
 using strag::MarchTables;
 
+// Upper bound on the Crank-Nicolson steps of one ray (sum over its segments of ceil(len / h_max)):
+// a 40 cm ray at h_max = 0.001 cm takes 4e4.
+constexpr double kMaxStepsPerRay = 1.0e6;
+
 __global__ void __launch_bounds__(64) straggling_march_kernel(int nray, const int* __restrict__ seg_ptr,
                                                             const int* __restrict__ seg_cell,
                                                             const double* __restrict__ seg_len,
@@ -233,6 +237,18 @@ dlra_status prepare_trace(const dlra_straggling_trace_args& a, HostTrace& h) {
     std::vector<double> lens;
     ray_segments(pts[r].data(), d, a, two_d, cells, lens);
     if (cells.empty()) continue;
+    // Crank-Nicolson steps of this ray: one device thread takes them one after the other, so a
+    // step length far below the voxel size would keep that thread busy for minutes
+    double steps = 0.0;
+    for (double l : lens) steps += std::max(1.0, std::ceil(l / a.h_max - 1e-12));
+    if (steps > kMaxStepsPerRay) {
+      char msg[200];
+      std::snprintf(msg, sizeof msg,
+                    "straggling trace: h_max = %g cm gives %.0f Crank-Nicolson steps on one ray (limit %.0f)", a.h_max,
+                    steps, kMaxStepsPerRay);
+      set_context_free_error(msg);
+      return DLRA_ERR_ARG;
+    }
     seg_cell.insert(seg_cell.end(), cells.begin(), cells.end());
     seg_len.insert(seg_len.end(), lens.begin(), lens.end());
     seg_ptr.push_back((int)seg_cell.size());
@@ -290,11 +306,15 @@ extern "C" dlra_status dlra_straggling_trace(const dlra_straggling_trace_args* a
   // device copies: tables, rays, work space (one slice per ray)
   const size_t per_ray = strag::work_per_ray(G);
   std::vector<void*> bufs;
+  cudaError_t copy_err = cudaSuccess;
   auto dev = [&](const void* src, size_t bytes) -> void* {
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
     bufs.push_back(p);
-    if (src) cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, st);
+    if (src) {
+      const cudaError_t e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess && copy_err == cudaSuccess) copy_err = e;
+    }
     return p;
   };
   MarchTables t;
@@ -320,7 +340,8 @@ extern "C" dlra_status dlra_straggling_trace(const dlra_straggling_trace_args* a
   double* scratch = (double*)dev(nullptr, sizeof(double) * per_ray * nray);
   bool ok = t.mass && t.adv && t.sipg && t.rem && t.SW && t.bin0 && t.nbin && t.bw && t.c0 && d_ptr && d_cell &&
             d_len && d_w && scratch;
-  if (ok) {
+  if (ok && copy_err != cudaSuccess) err = copy_err;
+  if (ok && err == cudaSuccess) {
     straggling_march_kernel<<<(nray + 63) / 64, 64, 0, st>>>(nray, d_ptr, d_cell, d_len, d_w, t, a.f_cell,
                                                              a.tau_cell, scratch, a.psi, a.e_u);
     err = cudaGetLastError();

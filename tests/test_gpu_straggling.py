@@ -13,7 +13,7 @@ from paper_2508_04484_gb300 import workloads as WL
 
 from .gpu_util import rel_l2
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="not yet run on a GB300")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
