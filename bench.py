@@ -1,18 +1,23 @@
 """Throughput of the low-rank collided-proton transport solve on GB300.
 
-One bench step is one whole transport solve of the workload: the CSDA ray trace
-of the beam, every energy step of the low-rank integrator (streaming BUG with RK4,
-implicit collided scattering, first-collision source, truncations) and the dose.
-Default workload: 64^3 voxels of 2 mm water, one 150 MeV pencil beam, Boltzmann
-screened-Rutherford scattering (eta = 1e-3, extended transport correction),
-P_15 (256 moments), fixed rank 20, 200 energy steps 150 -> 1 MeV, FP32 n-side
-arithmetic with FP64 reductions/factorisations.
+Headline workload: the 128^3 heterogeneous phantom (1.5 mm voxels, three base materials by the
+mixture model: water, cortical bone, lung; seeded ellipsoid inclusions), one 180 MeV pencil beam,
+Boltzmann screened-Rutherford scattering with the extended transport correction, P_21 (484
+moments), adaptive rank (truncation tolerance 1e-3 relative, at most 60), 358 energy steps
+180 -> 1 MeV, FP32 streaming stage and contractions with FP64 orthonormalisation (pivoted
+CholeskyQR2 factors on the cell side, Householder QR and Gram-Schmidt on the moment side).
+
+A bench step is a run of consecutive energy steps of the solve: with K timed steps each runs
+ceil(358 / K) energy steps, so the K timed steps together are one whole solve (the ray trace at
+the start of the first step, every energy step with its streaming BUG step, collided scattering,
+first-collision source and truncations, the dose read at the end of the last step). value =
+energy steps / s over the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the FP64 CPU oracle on the host cores, each step a bounded
-sample (a few energy steps) of the same workload. Under torchrun each rank runs
-its own copy of the workload (beams are independent: weak scaling); rank 0
+--impl reference times the FP64 CPU oracle on the host cores, each step one energy step of a
+bounded sample of the same workload (a 12^3 block of the phantom), scaled to the whole grid.
+Under torchrun each rank solves its own copy of the single-beam workload (weak scaling); rank 0
 prints one JSON line.
 """
 from __future__ import annotations
@@ -23,6 +28,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -32,22 +38,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "energy steps/s and cell·rank updates/s per GB300, % HBM roofline, vs plain"
 UNIT = "energy steps/s"
-WORKLOAD = "water_64cube_boltzmann"
+WORKLOAD = "phantom_128cube_adaptive"
+SECOND = "water_64cube_boltzmann"
+WORKLOADS = [WORKLOAD, SECOND, "phantom_48cube_8beams", "phantom_96cube_32beams", "phantom_64cube_8beams",
+             "slab_fp_40x40"]
+PRECISION_NAMES = {0: "FP64", 1: "FP32-mixed (FP32 stage, contractions, SVD and S-step; FP64 orthonormalisation)",
+                   2: "FP32-split (FP32 stage and contractions; FP64 orthonormalisation, truncation SVD and S-step)"}
 
 
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
+    p.add_argument("--precision", type=int, choices=[0, 1, 2], default=None,
+                   help="override the workload's precision (0 FP64, 1 FP32-mixed, 2 FP32-split)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-second", action="store_true", help="skip the 64^3 water line")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
-    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3], default=None,
-                   help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs), "
-                        "set after the autotuner")
+    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3, 4, 5], default=None,
+                   help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs, "
+                        "4 / 5 TMA-staged tensor cores, 128 / 256-cell bricks), set after the autotuner")
     p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1], default=None,
                    help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores), set after the autotuner")
     p.add_argument("--replicas", action="store_true",
@@ -56,8 +71,6 @@ def _args():
                    help="replay the energy steps from CUDA graphs (auto: on for multi-beam workloads)")
     p.add_argument("--energy-steps", type=int, default=0,
                    help="profiling only: stop each solve after this many energy steps")
-    p.add_argument("--workload", default=WORKLOAD,
-                   choices=[WORKLOAD, "phantom_48cube_8beams", "phantom_96cube_32beams", "phantom_128cube_adaptive"])
     return p.parse_args()
 
 
@@ -75,8 +88,11 @@ STAGE_KERNELS = {
     2: ("kstage_brick_kernel", "// Cell bricks of the staged streaming stage", None),
     3: ("kstage_pair_kernel", "// The streaming stage of kstage_kernel on the FP32 path with two",
         "// Cell bricks of the staged streaming stage"),
+    4: ("kstage_tma_kernel", None, None),
+    5: ("kstage_tma_kernel", None, None),
 }
-STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3}
+STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
+               "TMA tensor cores 256": 5}
 
 
 def stage_source_sha256(variant):
@@ -93,17 +109,17 @@ def stage_source_sha256(variant):
     return hashlib.sha256(src[i:j].encode()).hexdigest()
 
 
-def _stage_traffic(variant):
-    """DRAM bytes per launch of the streaming-stage kernel in use from the committed ncu summary,
-    or None when there is none or the kernel's source changed since that capture."""
+def _stage_traffic(variant, workload=WORKLOAD):
+    """DRAM bytes per launch of the streaming-stage kernel in use on this workload from the
+    committed ncu summary, or None when there is none or the kernel's source changed since."""
     name = STAGE_KERNELS[variant][0]
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
     if not os.path.exists(path):
         return None, None
     with open(path) as f:
-        d = json.load(f).get("kernels", {}).get(name)
+        d = json.load(f).get("workloads", {}).get(workload, {}).get("kernels", {}).get(name)
     if d is None:
-        return None, f"no capture of {name}"
+        return None, f"no capture of {name} on {workload}"
     h = stage_source_sha256(variant)
     if h is None or d.get("source_sha256") != h:
         return None, "kernel changed since the capture"
@@ -120,7 +136,8 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region (samples go
+    to a temporary file that is removed afterwards)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -129,12 +146,12 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="bench_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -152,7 +169,10 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        os.unlink(self.path)
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -177,49 +197,100 @@ def _dist():
     return ws, rank, local
 
 
-def _rank_stats(log, nsub, n):
-    """Cell-rank updates and streaming-stage work of one solve from its rank log."""
-    K = len(nsub)
+def _start_ranks(log):
+    """Rank at the start of every energy step of one solve from its rank log."""
+    K = len(log)
     r_start = np.zeros(K, dtype=np.int64)
     for k in range(1, K):
         a, b = log[k - 1]
         r_start[k] = b if b >= 0 else max(a, 0)
-    updates = int(np.sum(r_start) * n)
-    active = r_start > 0
-    stage_launches = int(np.sum(4 * np.asarray(nsub)[active]))
-    return r_start, updates, stage_launches
+    return r_start
 
 
-def cpu_baseline(cfg, mats, w, beams, budget_steps=1, k0=40):
-    """The FP64 oracle as it stands, on the host cores, for energy steps k0, k0 + 1, ... of the
-    workload started from a state at the workload's full rank (random orthonormal factors,
-    decaying singular values): the steady-state cost of a step, which most of the 200 steps pay
-    (the first steps, at rank 1-10, are far cheaper). Source from a single central ray."""
+def stage_work(cfg, r_start, nsub):
+    """Algorithmic bytes and flops of the streaming-stage launches of one solve: per cell and
+    launch (5r + 1) words (stage input, state and output columns of K, the next stage's scaled
+    input, rho^-1) and 2 nk r^2 + 6 nk r flops (the r x r mix of nk stencils and the stencils)."""
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    nk = 4 if cfg["ny"] == 1 and cfg["dy"] == 0 else 6
+    esize = 8 if cfg["precision"] == 0 else 4
+    act = r_start > 0
+    launches = 4 * np.asarray(nsub)[act]
+    r = r_start[act].astype(np.float64)
+    byts = float(np.sum(launches * n * (5 * r + 1) * esize))
+    flops = float(np.sum(launches * n * (2 * nk * r * r + 6 * nk * r)))
+    return int(np.sum(launches)), byts, flops
+
+
+def _oracle_block(cfg, mats, w, edge):
+    """The central edge^3 block of a 3-D workload's grid (same voxels and mixture weights)."""
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    i0, j0, k0 = (nx - edge) // 2, (ny - edge) // 2, 0
+    W = np.asarray(w).reshape(len(mats), nz, ny, nx)[:, k0:k0 + edge, j0:j0 + edge, i0:i0 + edge]
+    c = dict(cfg, nx=edge, ny=edge, nz=edge)
+    return c, W.reshape(len(mats), -1), (i0 * cfg["dx"], j0 * cfg["dy"], k0 * cfg["dz"])
+
+
+def _oracle_step_seconds(cfg, mats, w, beams, edge, k0, reps):
+    """Seconds of one FP64 oracle energy step k0 on the central edge^3 block of the workload, from a
+    state at the workload's rank (random orthonormal factors, decaying singular values), the source
+    of the workload's beam traced through the block; returns (times, the block's n_sub at k0)."""
     from oracle import dlra as ODL
     from oracle import problem as OP
     from oracle import raytrace as ORT
-    prob = OP.Problem(cfg, mats, w)
-    b = dict(beams[0], spot_sigma=0.0)
+    c, wb, off = _oracle_block(cfg, mats, w, edge)
+    prob = OP.Problem(c, mats, wb)
+    b = dict(beams[0])
+    b["pos"] = [b["pos"][0] - off[0], b["pos"][1] - off[1], b["pos"][2] - off[2]]
+    b["spot_sigma"] = min(float(b.get("spot_sigma", 0.0)), 0.1)
     r = ORT.trace(prob, b)
     src = [(r.psi, r.e_u, np.asarray(b["dir"]))]
-    rank = int(cfg["rank"])
-    rng = np.random.default_rng(0)
-    st = ODL.State(prob.n, prob.m)
-    st.X = np.linalg.qr(rng.standard_normal((prob.n, rank)))[0]
-    st.W = np.linalg.qr(rng.standard_normal((prob.m, rank)))[0]
-    st.S = np.diag(1e-3 * 0.8 ** np.arange(rank))
-    rc = ODL.RankControl(mode=cfg["rank_mode"], rank=cfg["rank"], tol=cfg["trunc_tol"], r_max=cfg["rank_max"])
-    t0 = time.perf_counter()
-    upd = 0
-    for k in range(k0, k0 + budget_steps):
-        upd += prob.n * st.r
-        ODL.step(prob, st, k, src, rc)
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": budget_steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "cell_rank_updates_per_s": upd / dt,
-            "sample": f"energy steps {k0}..{k0 + budget_steps - 1} of {WORKLOAD} from a rank-{rank} state "
-                      f"(source of one central ray), {dt:.1f} s, numpy/BLAS threads on {cores} cores"}
+    rank = int(cfg["rank_max"])
+    times = []
+    for rep in range(reps):
+        rng = np.random.default_rng(rep)
+        st = ODL.State(prob.n, prob.m)
+        st.X = np.linalg.qr(rng.standard_normal((prob.n, rank)))[0]
+        st.W = np.linalg.qr(rng.standard_normal((prob.m, rank)))[0]
+        st.S = np.diag(1e-3 * 0.9 ** np.arange(rank))
+        rc = ODL.RankControl(mode=OP.FIXED, rank=rank, r_max=rank)
+        t0 = time.perf_counter()
+        ODL.step(prob, st, k0, src, rc)
+        times.append(time.perf_counter() - t0)
+    return times, prob.n_sub(k0)
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(name, edge=16, k0=60, reps=2, one_core=True):
+    """The FP64 oracle as it stands, on the host cores: energy step k0 of the workload on its central
+    edge^3 block, scaled to the whole grid by the cell count and the sub-step count of step k0."""
+    cfg, mats, w, beams = _workload(name)
+    from oracle import problem as OP
+    prob_full_nsub = OP.Problem(cfg, mats, w).n_sub(k0)
+    times, nsub_b = _oracle_step_seconds(cfg, mats, w, beams, edge, k0, reps)
+    n_full = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    scale = n_full / edge ** 3 * prob_full_nsub / max(nsub_b, 1)
+    out = {"value": 1.0 / (min(times) * scale), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+           "min_s": min(times), "median_s": float(np.median(times)), "runs": reps,
+           "sample": f"energy step {k0} of {name} on its central {edge}^3 block (FP64 oracle, rank "
+                     f"{cfg['rank_max']} state, {nsub_b} RK4 sub-steps), scaled by the cell count "
+                     f"({n_full}/{edge ** 3}) and the workload's sub-steps at that step ({prob_full_nsub}); "
+                     f"min of {reps} runs, numpy/BLAS threads on {_cores()} cores"}
+    if one_core:
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "t, nb = bench._oracle_step_seconds(*bench._workload(%r), %d, %d, 1); print(json.dumps([t, nb]))"
+                % (ROOT, name, edge, k0))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+            t1, _ = json.loads(r.stdout.strip().splitlines()[-1])
+            out["one_core"] = {"value": 1.0 / (min(t1) * scale), "seconds": min(t1)}
+        except Exception as e:  # the 1-core figure is context only
+            out["one_core"] = {"error": str(e)[:200]}
+    return out
 
 
 def _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=False):
@@ -261,29 +332,79 @@ def _plain_vs_batched(cfg, mats, w, beams, K, args):
             "batched": "one lane (work space + stream pair) per beam, energy steps replayed from a CUDA graph"}
 
 
+def _config_block(name, cfg, beams, K):
+    return {"workload": name, "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}", "voxel_mm": 10.0 * cfg["dx"],
+            "beams": len(beams), "beam_MeV": [round(b["energy"], 1) for b in beams][:4],
+            "collision": "boltzmann screened-Rutherford + ETC" if cfg["collision"] == 1 else "fokker-planck",
+            "sh_degree": cfg["N"], "moments": (cfg["N"] + 1) ** 2,
+            "rank": ("adaptive tol %g, max %d" % (cfg["trunc_tol"], cfg["rank_max"])) if cfg["rank_mode"] == 1
+            else "fixed %d" % cfg["rank"],
+            "energy_steps": K, "precision": PRECISION_NAMES[cfg["precision"]]}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    cfg, mats, w, beams = _workload()
+    name = args.workload
+    cfg, mats, w, beams = _workload(name)
+    from oracle import problem as OP
+    edge, k0 = 12, 60
+    nsub_full = OP.Problem(cfg, mats, w).n_sub(k0)
+    n_full = cfg["nx"] * cfg["ny"] * cfg["nz"]
     samples = []
+    nsub_b = 1
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(cfg, mats, w, beams, budget_steps=1)
+        t, nsub_b = _oracle_step_seconds(cfg, mats, w, beams, edge, k0, 1)
         if i >= args.warmup:
-            samples.append(cb)
-    val = float(np.mean([s["value"] for s in samples]))
-    ms = 1000.0 / val * cfg["n_steps"]
+            samples.append(t[0])
+    scale = n_full / edge ** 3 * nsub_full / max(nsub_b, 1)
+    val = float(args.steps / (np.sum(samples) * scale))
+    sample = (f"each step: energy step {k0} of {name} on its central {edge}^3 block (FP64 oracle, rank "
+              f"{cfg['rank_max']} state, {nsub_b} RK4 sub-steps), scaled by the cell count ({n_full}/{edge ** 3}) "
+              f"and the workload's sub-steps at that step ({nsub_full}); numpy/BLAS threads on {_cores()} cores")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "voxels": "64x64x64", "voxel_mm": 2.0, "sh_degree": 15,
-                       "rank": 20, "energy_steps": 200, "beams": 1,
-                       "reference_sample": "each step: one energy step of the FP64 oracle at full rank"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": samples[0]["cores"],
-                             "sample": samples[0]["sample"]},
+            "config": dict(_config_block(name, cfg, beams, cfg["n_steps"]), precision="FP64 (oracle)",
+                           reference_sample=sample),
+            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": _cores(), "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def _second_line(args, stream):
+    """Whole solves of the 64^3 water workload (P_15, rank 20) at the FP32-split precision."""
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    cfg, mats, w, beams = _workload(SECOND)
+    cfg = dict(cfg, precision=2)
+    s = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
+    tuned = s.autotune() if not args.no_autotune else None
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    dose = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    K = cfg["n_steps"]
+    times = []
+    with torch.cuda.stream(stream):
+        for i in range(5):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.reset(retrace=True)
+            s.step(K)
+            s.dose(out=dose)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 2:
+                times.append(e0.elapsed_time(e1))
+    s.close()
+    ms = float(np.mean(times))
+    return {"workload": SECOND, "value": K / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
+            "config": _config_block(SECOND, cfg, beams, K), "steps": "3 whole solves after 2 warm-up solves",
+            "stage_variant": tuned["stage_variant"] if tuned else None}
 
 
 def main():
@@ -302,9 +423,14 @@ def main():
     from paper_2508_04484_gb300 import build as B
     from paper_2508_04484_gb300 import dlra as D
     B.build()
-    cfg, mats, w, beams = _workload(args.workload)
+    name = args.workload
+    cfg, mats, w, beams = _workload(name)
+    if args.precision is not None:
+        cfg = dict(cfg, precision=args.precision)
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     K = cfg["n_steps"] if args.energy_steps <= 0 else min(args.energy_steps, cfg["n_steps"])
+    steps = max(1, args.steps)
+    chunk = max(1, math.ceil(K / steps))
     vs_plain = None
     if len(beams) > 1 and ws == 1:
         vs_plain = _plain_vs_batched(cfg, mats, w, beams, K, args)
@@ -317,16 +443,25 @@ def main():
     my_beams = MG.shard_beams(beams, rank, ws) if shard else beams
     solver = D.Solver(dict(cfg, max_concurrent_beams=min(len(my_beams), 32)), mats, w, my_beams,
                       stream=stream.cuda_stream)
-    nsub = solver.substeps()
+    nsub = solver.substeps()[:K]
     dose = torch.zeros(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    cursor = [0]
 
-    def one_solve():
-        solver.reset(retrace=True)
-        solver.step(K)
-        solver.dose(out=dose)
-        if shard:
-            MG.reduce_dose(dose)
+    def bench_step():
+        """The next chunk of energy steps of the current solve (a new solve starts with a reset and
+        ray trace, the last chunk of a solve ends with the dose read)."""
+        if cursor[0] == 0:
+            solver.reset(retrace=True)
+        ne = min(chunk, K - cursor[0])
+        solver.step(ne)
+        cursor[0] += ne
+        if cursor[0] >= K:
+            solver.dose(out=dose)
+            if shard:
+                MG.reduce_dose(dose)
+            cursor[0] = 0
+        return ne
 
     tuned = solver.autotune() if not args.no_autotune else None
     if args.stage_kernel is not None:
@@ -335,15 +470,16 @@ def main():
         solver.set_stencil_gram_kernel(args.stencil_gram_kernel)
     use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
     solver.set_graphs(use_graphs)
-    for _ in range(args.warmup):
-        one_solve()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            bench_step()
+        while cursor[0] != 0:      # finish the warm-up solve: the timed steps start a new solve
+            bench_step()
     torch.cuda.synchronize()
     log = solver.rank_log(0)[:K]
-    nsub = nsub[:K]
-    r_start, updates, stage_launches = _rank_stats(log, nsub, n)
-    # the ray trace alone (part of every timed solve): reset with a fresh trace, best of three
-    # (after the rank log of the warm-up solve is read: a reset clears it; every timed solve
-    # starts with the same reset)
+    r_start = _start_ranks(log)
+    updates = int(np.sum(r_start) * n)
+    # the ray trace alone (part of the first timed step): a reset with a fresh trace, best of three
     rt_ms = []
     for _ in range(3):
         t0 = time.perf_counter()
@@ -351,8 +487,9 @@ def main():
         torch.cuda.synchronize()
         rt_ms.append((time.perf_counter() - t0) * 1000.0)
     raytrace_ms = min(rt_ms)
+    cursor[0] = 0
     clocks = Clocks(dev.index)
-    # ---- timed region: K whole solves, L2 flushed between them ----
+    # ---- timed region: K bench steps = whole solves, L2 flushed between steps ----
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -361,14 +498,14 @@ def main():
     # individual kernels, so with graphs they come from one profiled solve afterwards
     solver.set_profiling(not use_graphs)
     launches0 = solver.launch_count()
-    times = []
+    times, esteps = [], 0
     with torch.cuda.stream(stream):
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one_solve()
+            esteps += bench_step()
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -380,30 +517,29 @@ def main():
     if use_graphs:
         solver.set_profiling(True)
         with torch.cuda.stream(stream):
-            one_solve()
+            solver.reset(retrace=True)
+            solver.step(K)
         torch.cuda.synchronize()
     stage_ms, stage_count = solver.kernel_stats()
     solver.set_profiling(False)
-    ms_per_solve = float(np.sum(times) / args.steps)
+    total_ms = float(np.sum(times))
     if ws > 1:
-        t = torch.tensor([ms_per_solve], device=dev)
+        t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_solve = float(t.item())
-    value = (1 if shard else ws) * K / (ms_per_solve / 1000.0)
-    updates_per_s = (1 if shard else ws) * updates / (ms_per_solve / 1000.0)
+        total_ms = float(t.item())
+    solves = esteps / K
+    value = (1 if shard else ws) * esteps / (total_ms / 1000.0)
+    updates_per_s = (1 if shard else ws) * updates * solves / (total_ms / 1000.0)
     # ---- roofline of the dominant kernel: fused streaming stage (stencil x r-by-r mix) ----
-    nk = 4 if cfg["ny"] == 1 and cfg["dy"] == 0 else 6
-    esize = 4 if cfg["precision"] == 1 else 8
-    act = r_start > 0
-    per_solve_launches = int(np.sum(4 * np.asarray(nsub)[act]))
-    bytes_solve = float(np.sum((4 * np.asarray(nsub) * n * (3 * r_start + 1) * esize)[act]))
-    flops_solve = float(np.sum((4 * np.asarray(nsub) * n * 2 * nk * r_start.astype(np.float64) ** 2)[act]))
+    nl_solve, bytes_solve, flops_solve = stage_work(cfg, r_start, nsub)
     avg_launch_ms = stage_ms / max(stage_count, 1)
-    avg_bytes = bytes_solve / max(per_solve_launches, 1)
-    avg_flops = flops_solve / max(per_solve_launches, 1)
+    avg_bytes = bytes_solve / max(nl_solve, 1)
+    avg_flops = flops_solve / max(nl_solve, 1)
     peaks, src = _peaks()
     hbm_peak = float(peaks["hbm_gbs"])
-    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # FFMA, TFLOP/s
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # FFMA, TFLOP/s
     gbs = avg_bytes / (avg_launch_ms / 1000.0) / 1e9
     tfs = avg_flops / (avg_launch_ms / 1000.0) / 1e12
     frac_hbm = gbs / hbm_peak
@@ -412,59 +548,60 @@ def main():
         STAGE_NAMES.get(tuned["stage_variant"], 0) if tuned else 0)
     if variant == 3 and cfg["nx"] % 2:
         variant = 0
-    traffic, traffic_note = _stage_traffic(variant)
-    # the same launch measured by its DRAM bytes (ncu capture) over its CUDA-event time
+    traffic, traffic_note = _stage_traffic(variant, name)
     traffic_gbs = traffic / (avg_launch_ms / 1000.0) / 1e9 if traffic else None
     kname = f"{STAGE_KERNELS[variant][0]} (fused RK4 streaming stage: stencil + r x r mix)"
+    common = {"traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
+              "algorithmic_flops_per_launch": avg_flops, "kernel": kname, "launches_per_solve": nl_solve,
+              "avg_launch_us": avg_launch_ms * 1000.0,
+              "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
+              "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
+              "counts": "per cell and launch (5r + 1) words and 2 nk r^2 + 6 nk r flops at the step's rank"}
     if frac_alu >= frac_hbm:
-        roof = {"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
-                "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
-                "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
-                "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
-                "achieved_gbs": gbs, "hbm_frac": frac_hbm, "avg_launch_us": avg_launch_ms * 1000.0,
-                "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None}
+        roof = dict({"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz} MHz ({src} clock)",
+                     "achieved_gbs": gbs, "hbm_frac": frac_hbm}, **common)
     else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
-                "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,
-                "algorithmic_flops_per_launch": avg_flops, "kernel": kname,
-                "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "alu_frac": frac_alu,
-                "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
-                "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
-                "avg_launch_us": avg_launch_ms * 1000.0}
+        roof = dict({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                     "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "alu_frac": frac_alu}, **common)
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if (rank == 0 or ws > 1) and not args.no_e2e:
         w_host = np.ascontiguousarray(w, dtype=np.float64)
         dose_host = np.zeros(n)
-        e2e_times = []
-        for i in range(2):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s2 = D.Solver(cfg, mats, w_host, my_beams, stream=stream.cuda_stream)
-            s2.step(K)
-            s2.dose(out=dose_host)
-            e2e_times.append(time.perf_counter() - t0)
-            s2.close()
-        e2e_s = min(e2e_times)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = D.Solver(cfg, mats, w_host, my_beams, stream=stream.cuda_stream)
+        if tuned:
+            s2.set_stage_kernel(variant)
+        s2.step(K)
+        s2.dose(out=dose_host)
+        e2e_s = time.perf_counter() - t0
+        s2.close()
         e2e = {"value": (1 if shard else ws) * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w_host.nbytes),
                "d2h_bytes_per_step": int(dose_host.nbytes),
                "includes": "context creation with angular tables, host->device mixture weights, ray trace, "
-                           "all energy steps, dose read back to host"}
-    # ---- reverse sweep (gradients of L = |e|^2 / 2 w.r.t. beam and mixture weights), outside the timed region ----
+                           "all energy steps, dose read back to host (one whole solve)"}
+    second = None
+    if rank == 0 and ws == 1 and not args.no_second and name == WORKLOAD:
+        second = _second_line(args, stream)
+    # ---- reverse sweep of the 64^3 water workload (gradients of L = |e|^2 / 2), outside the timed region ----
     adj = None
     if rank == 0 and ws == 1 and not args.no_adjoint:
+        cfg3, mats3, w3, beams3 = _workload(SECOND)
+        K3 = cfg3["n_steps"]
         interval = 16
-        s3 = D.Solver(cfg, mats, w, beams, stream=stream.cuda_stream)
+        s3 = D.Solver(cfg3, mats3, w3, beams3, stream=stream.cuda_stream)
         s3.enable_adjoint(interval)
-        g_dev = torch.zeros(n, dtype=torch.float64, device=dev)
-        dw_dev = torch.empty((len(mats), n), dtype=torch.float64, device=dev)
+        n3 = cfg3["nx"] * cfg3["ny"] * cfg3["nz"]
+        g_dev = torch.zeros(n3, dtype=torch.float64, device=dev)
+        dw_dev = torch.empty((len(mats3), n3), dtype=torch.float64, device=dev)
         fwd, bwd = [], []
         for _ in range(2):
             s3.reset(retrace=True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s3.step(K)
+            s3.step(K3)
             s3.dose(out=g_dev)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -474,35 +611,34 @@ def main():
             fwd.append(t1 - t0)
             bwd.append(t2 - t1)
         s3.close()
-        adj = {"ms_per_backward": 1000.0 * min(bwd), "ms_forward_with_checkpoints": 1000.0 * min(fwd),
-               "backward_over_forward": min(bwd) / (ms_per_solve / 1000.0), "checkpoint_interval": interval,
-               "loss": "|e|^2/2 (dL/de = e)", "outputs": "dL/dweight per beam, dL/dw per material and cell",
+        adj = {"workload": SECOND, "ms_per_backward": 1000.0 * min(bwd),
+               "ms_forward_with_checkpoints": 1000.0 * min(fwd), "backward_over_forward": min(bwd) / min(fwd),
+               "checkpoint_interval": interval, "loss": "|e|^2/2 (dL/de = e)",
+               "outputs": "dL/dweight per beam, dL/dw per material and cell",
                "timing": "host wall clock around synchronising calls, best of two passes"}
     cb = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cfg_c, mats_c, w_c, beams_c = _workload()
-        cb = cpu_baseline(cfg_c, mats_c, w_c, beams_c)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and len(beams) == 1 and cfg["ny"] > 1:
+        cb = cpu_baseline(name)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": True,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
                 "scaling": "strong" if shard else "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if cfg["precision"] == 1 else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "voxels": "64x64x64", "voxel_mm": 2.0, "material": "water",
-                           "beam_MeV": 150, "collision": "boltzmann screened-Rutherford eta=1e-3 + ETC",
-                           "sh_degree": 15, "moments": 256, "rank": 20, "energy_steps": K,
-                           "step": "one whole solve (ray trace + all energy steps + dose)",
-                           "l2": "flushed (256 MB write) between timed solves"},
+                "vs_baseline": None, "dtype": "f64" if cfg["precision"] == 0 else "f32+f64", "data": "synthetic",
+                "config": dict(_config_block(name, cfg, beams, K),
+                               step=f"{chunk} consecutive energy steps of the solve; {steps} steps = "
+                                    f"{solves:g} whole solve(s) (ray trace, {K} energy steps, dose read)",
+                               l2="flushed (256 MB write) between timed steps; the factors exceed L2"),
                 "cell_rank_updates_per_s": updates_per_s,
                 "energy_steps_per_s": value,
+                "ms_per_solve": total_ms / solves,
                 "gpu_launches": int(launches),
                 "roofline": roof, "clocks": ck, "e2e": e2e, "cpu_baseline": cb,
-                "vs_plain": vs_plain, "adjoint": adj, "cuda_graphs": use_graphs, "autotune": tuned,
+                "vs_plain": vs_plain, "second": second, "adjoint": adj, "cuda_graphs": use_graphs,
+                "autotune": tuned,
+                "ranks": {"mean": float(np.mean(r_start)), "max": int(np.max(r_start))},
                 "raytrace_ms": {"value": raytrace_ms, "timing": "host wall clock around a reset with a fresh "
-                                "ray trace of every beam and a synchronise, best of three; included in each step"}}
-        if args.workload != WORKLOAD:
-            line["config"] = {"workload": args.workload, "beams": len(beams), "voxels": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}",
-                              "sh_degree": cfg["N"], "rank_max": cfg["rank_max"], "energy_steps": K,
-                              "step": "one whole solve of all beams"}
+                                "ray trace of every beam and a synchronise, best of three; inside the first step"}}
+        if len(beams) > 1:
             line["beam_energy_steps_per_s"] = value * len(beams)
         print(json.dumps(line))
     solver.close()

@@ -57,7 +57,11 @@ enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1, DLRA_FP32_SPLIT = 2 };
  *  sh_degree              : N, m = (N+1)^2 moments (Sec. 3.3.1); 1 <= N <= 31.
  *  collision              : DLRA_FOKKER_PLANCK or DLRA_BOLTZMANN (Sec. 2.1).
  *  transport_correction   : 1 = extended transport correction of the Boltzmann
- *                           moments, sigma_l - sigma_{N+1} (Sec. 3.3.1).
+ *                           moments, sigma_l - sigma_{N+1} (Sec. 3.3.1); 2 = the same
+ *                           and, for Fokker-Planck, the delta-function corrected
+ *                           moments of Landesman and Morel (Sec. 3.3.1): G_l =
+ *                           (xi_1/2) [(N+1)(N+2) - l(l+1)], Sigma_t = G_0 (the uncollided
+ *                           beam is then removed into the collided source); 0 = none.
  *  rank_mode, rank,       : truncation (Sec. 2.2). FIXED keeps min(rank, numerical rank);
  *  rank_max, trunc_tol      ADAPTIVE keeps the smallest r with sum_{i>r} sigma_i <=
  *                           trunc_tol * ||sigma||_2 clamped to [1, rank_max]; SCHEDULE
@@ -72,7 +76,9 @@ enum { DLRA_FP64 = 0, DLRA_FP32_MIXED = 1, DLRA_FP32_SPLIT = 2 };
  *  precision              : DLRA_FP64, or DLRA_FP32_MIXED (FP32 n-side data and
  *                           arithmetic, FP64 reductions, factorisations and S), or
  *                           DLRA_FP32_SPLIT (as DLRA_FP32_MIXED with the 2r x 2r
- *                           truncation SVD and the Galerkin S-step in FP64 arithmetic).
+ *                           truncation SVD, the Galerkin S-step, the Householder QR of
+ *                           the collided L-step and the W-side augmentation in FP64
+ *                           arithmetic; W is stored in FP32).
  *  bk_p, bk_alpha         : Bragg-Kleeman water stopping power S_w(E) = E^(1-p)/(p alpha).
  *  t100                   : water scattering power at 100 MeV, T_w(E) = t100 (100/E)^2.
  *  max_concurrent_beams   : beams advanced concurrently (one work space and stream pair
@@ -224,18 +230,23 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel). Needs materials and a beam; synchronises; drops captured graphs. report (optional,
- * 16 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 per cell, 1 tensor cores, 2 brick, 3 cell
- * pairs), Gram block target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core
- * stencil Gram, the chosen stencil-Gram kernel (0 FMA, 1 tensor cores) and ms of the cell-pair
- * stage (-1 where not applicable). */
+ * 20 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 .. 5 as dlra_set_stage_kernel), Gram block
+ * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
+ * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
+ * the TMA-staged tensor-core stages with 128- and 256-cell bricks, two zeros (-1 where not
+ * applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
  * 1 the tensor-core kernel of dlra_set_tensor_cores (FP32 path; the FMA kernel on FP64),
  * 2 one block per 256-cell brick with the stencil inputs staged in shared memory, 3 two
- * x-adjacent cells per thread with packed FP32x2 FMAs (FP32 path with nx even; else variant 0).
- * Same results up to rounding; dlra_autotune picks among them. */
+ * x-adjacent cells per thread with packed FP32x2 FMAs (FP32 path with nx even; else variant 0),
+ * 4 / 5 the r x r mix on the tensor cores (tcgen05.mma kind::tf32 with high/low TF32 splits,
+ * FP32 accuracy) with each chunk of four input columns of a 128- / 256-cell brick and its
+ * two-cell halo staged by one TMA copy (FP32 path, 3-D, nx and the cell count multiples of 4,
+ * rank capacity >= 32; else variant 0). Same results up to rounding; dlra_autotune picks among
+ * them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):
@@ -304,11 +315,15 @@ dlra_status dlra_kstep(const dlra_kstep_args* args);
 /* The same K-step as dlra_kstep for callers that cannot allocate device memory
  * (the paper has no counterpart; this is a library-usage variant). Its work space
  * is a static device array of 32 MiB held by every GPU that loads the library
- * until the process exits; problems whose work space (3 n rcap + 6 rcap^2 FP32
- * words, rcap = r rounded up to 4, 8, ..., 24, 32, 40, 48 or 64) exceeds it are
- * rejected with DLRA_ERR_ARG and a message naming both sizes. The first call on
- * each device looks up the array's device address with that device current; make
- * that first call before any stream capture. Every call uses the whole array and
+ * until the process exits; problems whose work space exceeds it are rejected with
+ * DLRA_ERR_ARG and a message naming both sizes. The work space is 3 n rcap +
+ * 2 nact rcap^2 FP32 words (nact = 2 on an x-z slab, 3 in 3-D; rcap = r rounded
+ * up to 4, 8, ..., 24, 32, 40, 48 or 64) plus up to 256 bytes of alignment per
+ * buffer and one rank word. The first call on each device looks up the array's
+ * device address with that device current and keeps it for the process; make
+ * that first call before any stream capture. A cudaDeviceReset (or any other
+ * teardown of the device's primary context) unloads the array, so the entry
+ * point must not be called on that device afterwards in the same process. Every call uses the whole array and
  * writes all of it that it reads (nothing needs to start at zero); calls that
  * overlap on the GPU (different streams, threads or processes sharing a context)
  * race on it. Enqueued on cuda_stream without synchronising; calls no cudaMalloc
@@ -383,7 +398,8 @@ dlra_status dlra_straggling_tables(const dlra_straggling_args* args, double* mas
  * straggling = 0 gives the CSDA limit. Beam: spot grid of pitch min(delta)/4 within 3.5
  * spot_sigma with Gaussian weights, initial energy distribution a Gaussian of energy_sigma
  * (a delta for 0) projected on the DG space. n_elem >= 1 with at most 8 energy bins
- * overlapping one element. */
+ * overlapping one element; at most 1e6 Crank-Nicolson steps on one ray (the sum over its voxel
+ * segments of ceil(length / h_max)), else DLRA_ERR_ARG before any launch. */
 typedef struct {
   int32_t nx, ny, nz;
   double dx, dy, dz;
@@ -406,8 +422,21 @@ typedef struct {
  * thread per ray marching the block-tridiagonal system with FP64 Thomas elimination.
  * Overwrites psi and e_u; allocates its tables and work space (3 G x 4 + 18 G doubles per ray)
  * and frees them; synchronises cuda_stream. Errors: DLRA_ERR_ARG, DLRA_ERR_OOM, DLRA_ERR_CUDA
- * (dlra_last_error(NULL)). Not yet run on a GB300 (its tests are skipped). */
+ * (dlra_last_error(NULL)); a failed host-to-device copy returns DLRA_ERR_CUDA before the
+ * launch. */
 dlra_status dlra_straggling_trace(const dlra_straggling_trace_args* args);
+
+/* enable = 1: the beams of this context share one low-rank state (the paper's multi-beam
+ * solve, Sec. 4.3), instead of one state per beam. Each energy step streams and scatters
+ * the joint state once and adds the first-collision sources of all beams that have one,
+ * each beam's rank-M factor (M materials) scaled by its weight, stacked into one source of
+ * rank M x (beams) (at most the rank capacity; DLRA_ERR_ARG at the next dlra_step otherwise).
+ * The collided deposit is the joint state's (weights included); the uncollided deposits
+ * enter times their beam's weight. dlra_rank_log(ctx, 0, ...) gives the joint state's ranks;
+ * dlra_set_beam_weight changes a beam's weight for the next solve (the source uses it).
+ * Direct launches only (dlra_set_graphs has no effect); no reverse sweep. Call before the
+ * first step; DLRA_ERR_STATE otherwise. */
+dlra_status dlra_set_joint(dlra_ctx* ctx, int32_t enable);
 
 /* Kernel launches issued by this context so far (for launch accounting). */
 int64_t dlra_launch_count(const dlra_ctx* ctx);

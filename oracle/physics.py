@@ -17,7 +17,13 @@ elements) is not available. The synthetic stand-ins, all stated as inputs:
 * base material i: S_i = rho_i s_i S_w(E), xi_{1;i} = rho_i kappa_i T_w(E) / 2;
 * Boltzmann kernel of material i: screened Rutherford
   Sigma_{s;i}(E, mu) = C_i(E) / (1 - mu + 2 eta_i)^2, with C_i fixed by xi_{1;i};
-* extended transport correction (Sec. 3.3.1, flag): sigma_l <- sigma_l - sigma_{N+1}.
+* extended transport correction (Sec. 3.3.1, flag): sigma_l <- sigma_l - sigma_{N+1};
+* the delta-function corrected expansion of the Fokker-Planck moments (Sec. 3.3.1, the
+  correction of Landesman and Morel; flag value 2): the moments are shifted by the same
+  constant so that the degree N+1 moment vanishes, G_l = (xi_1/2) [(N+1)(N+2) - l(l+1)],
+  with Sigma_t = G_0 = (xi_1/2)(N+1)(N+2); the self-scattering G_l - Sigma_t is unchanged.
+  These are the small-screening limit of the screened-Rutherford moments under the extended
+  transport correction (pinned in tests/test_oracle_physics.py).
 
 Every moment here is computed by quadrature of its defining integral. Pins
 (tests/test_oracle_physics.py): the closed forms sigma_0 = pi C / (eta (1+eta))
@@ -122,6 +128,8 @@ class PhysicsTables:
         self.N = N
         self.collision = collision
         self.etc = bool(transport_correction) and collision == BOLTZMANN
+        # transport_correction == 2: delta-function corrected Fokker-Planck moments
+        self.fp_delta = int(transport_correction) == 2 and collision != BOLTZMANN
         self.p = p
         self.alpha = alpha
         self.t100 = t100
@@ -150,7 +158,8 @@ class PhysicsTables:
 
         Boltzmann: G_l = sigma_l and Sigma_t = G_0 (Sec. 3.3.1), both shifted by
         -sigma_{N+1} under the extended transport correction.
-        Fokker-Planck: G_l = -(xi_1/2) l (l+1), Sigma_t = 0 (Gamma_out = 0, Sec. 3.1).
+        Fokker-Planck: G_l = -(xi_1/2) l (l+1), Sigma_t = 0 (Gamma_out = 0, Sec. 3.1); with the
+        delta-function correction G_l = (xi_1/2) [(N+1)(N+2) - l(l+1)] and Sigma_t = G_0.
         """
         if self.collision == BOLTZMANN:
             sig = self.boltzmann_moments(i, E)
@@ -159,7 +168,11 @@ class PhysicsTables:
                 G = G - sig[self.N + 1]
             return G, G[0]
         l = np.arange(self.N + 1, dtype=np.float64)
-        return -0.5 * self.xi1(i, E) * l * (l + 1), 0.0
+        xi = self.xi1(i, E)
+        if self.fp_delta:
+            G = 0.5 * xi * ((self.N + 1) * (self.N + 2) - l * (l + 1))
+            return G, G[0]
+        return -0.5 * xi * l * (l + 1), 0.0
 
     def self_scatter(self, i, E):
         """G_{i,l} - Sigma_{t,i}: the collided self-scattering eigenvalue per degree."""
@@ -174,10 +187,12 @@ class PhysicsTables:
         """Uncollided removal Sigma_{t,i} (Gamma_out, Sec. 3.1); E may be an array.
 
         Boltzmann: Sigma_t = G_0 = sigma_0 (minus sigma_{N+1} under the correction);
-        Fokker-Planck: 0.
+        Fokker-Planck: 0, or (xi_1/2)(N+1)(N+2) with the delta-function correction.
         """
         E = _num(E)
         if self.collision != BOLTZMANN:
+            if self.fp_delta:
+                return 0.5 * self.xi1(i, E) * (self.N + 1) * (self.N + 2)
             return np.zeros_like(E)
         s, xi = self._unit[i]
         C = self.xi1(i, E) / xi

@@ -16,6 +16,8 @@
 // The stopping power of the mixture is S(x, E) = rho_s(x) S_w(E): every base
 // material has the water energy dependence, so S^-1 = rho_s^-1 c(t) with the
 // scalar c(t) = 1/S_w(E(t)) folded into the Horner coefficients.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +35,7 @@
 #include "device.cuh"
 #include "kernels.h"
 #include "kstage_tc.cuh"
+#include "kstage_tma.cuh"
 #include "tables.h"
 
 using namespace dlra;
@@ -73,6 +76,17 @@ __global__ void src_vec_kernel(const T* __restrict__ w, const double* __restrict
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double ps = psi[i];
+  for (int j = 0; j < M; ++j) A[(long long)j * n + i] = T((double)w[(long long)j * n + i] * ps);
+}
+
+// A[:, col0 + j] = scale w_j(x) psi(x), j < M: one beam's rank-M source factor placed among the
+// stacked factors of a joint state
+template <typename T>
+__global__ void src_vec_scaled_kernel(const T* __restrict__ w, const double* __restrict__ psi, long long n, int M,
+                                      double scale, T* __restrict__ A) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double ps = scale * psi[i];
   for (int j = 0; j < M; ++j) A[(long long)j * n + i] = T((double)w[(long long)j * n + i] * ps);
 }
 
@@ -164,14 +178,41 @@ __global__ void kstep_store(const float* __restrict__ y, long long n, int r, flo
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
+// out[e] = T(in[e])
+template <typename T>
+__global__ void convert_kernel(const double* __restrict__ in, long long cnt, T* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < cnt) out[e] = T(in[e]);
+}
+
 // ---------------------------------------------------------------------------
 // launch helpers for the tiled product and the Gram reduction
 // ---------------------------------------------------------------------------
+// Multiprocessors of the current device (queried once per device; 152 on a GB300).
+int device_sms() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
+    }
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
 // Launch geometry chosen by dlra_autotune for the context being stepped on this thread.
 struct Tuning {
   int gram_blocks = 1216;     // target number of blocks of the Gram reductions (x the 2-D tile grid)
-  int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x 152 blocks
-  int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA
+  int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x SMs blocks
+  int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA,
+                              // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks
   int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
 };
@@ -216,7 +257,8 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
     if (ncols_j <= 2 && rows >= 4096) {
       // a few columns (the source step's rank-M updates): a bandwidth-bound reduction
       // at least eight rows per thread: the block reduction at the end costs ~5 x 32 shuffles
-      const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((rows + 2047) / 2048, 152 * 2));
+      const unsigned gx =
+          (unsigned)std::max<long long>(1, std::min<long long>((rows + 2047) / 2048, 2LL * device_sms()));
       const dim3 grid(gx, (unsigned)((acap + 31) / 32));
       if (ncols_j == 1)
         gram_narrow_kernel<T, 1><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j,
@@ -250,9 +292,67 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
 // rank capacities with a compiled streaming-stage kernel
 constexpr int kRankCaps[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
 
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query: the library
+// links only the runtime)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The streaming-stage input (rcap columns of ld floats, each an nx x ny x nz grid, x fastest)
+// as a 4-D tensor for TMA, box 16 x box_y x 8 x 4 (x, y, z, column). Needs nx and ld multiples
+// of 4 and a 16-byte aligned base (the tensor map's stride and address rules).
+bool stage_tensor_map(CUtensorMap* m, const float* vin, const Geo& g, long long ld, int rcap, int box_y) {
+  if (g.nx % 4 != 0 || ld % 4 != 0 || ((uintptr_t)vin & 15u) != 0 || g.nact != 3) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)rcap};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nxy * 4, (cuuint64_t)ld * 4};
+  const cuuint32_t box[4] = {16, (cuuint32_t)box_y, 8, 4};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(vin), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the TMA-staged tensor-core stage at a rank capacity and brick (FP32, 3-D, rcap >= 32);
+// false when the grid or the buffers do not meet its layout rules (the caller falls back)
+template <int RM, int TILES>
+bool kstage_tma_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                       const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                       int* err) {
+  using C = KsTma<RM, TILES>;
+  CUtensorMap m;
+  if (!stage_tensor_map(&m, vin, g, n, RM, C::BY)) return false;
+  cudaFuncSetAttribute(kstage_tma_kernel<RM, TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  kstage_tma_kernel<RM, TILES><<<kstage_tma_grid<RM, TILES>(g), C::THREADS, C::SMEM, st>>>(
+      m, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err);
+  return true;
+}
+
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
                    const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant) {
+  if constexpr (sizeof(T) == 4 && NACT == 3 && RM >= 32) {
+    if (variant == 4 || variant == 5) {
+      const bool done = variant == 4 ? kstage_tma_launch<RM, 1>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
+                                                                beta, last, err)
+                                     : kstage_tma_launch<RM, 2>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
+                                                                beta, last, err);
+      if (done) return;
+      variant = 0;
+    }
+  }
+  if (variant >= 4) variant = 0;
   if (variant == 2) {
     using Bk = Brick<NACT>;
     const size_t smem = ((size_t)2 * NACT * RM * RM + 2 * Bk::HALO) * sizeof(T);
@@ -345,7 +445,7 @@ void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, in
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   per_sm = std::max(per_sm, 1);
   const int gx = (int)std::max(
-      1LL, std::min(chunks, (long long)std::max(1, 152 * per_sm * tuning().gs_waves_x2 / 2 / nslice)));
+      1LL, std::min(chunks, (long long)std::max(1, device_sms() * per_sm * tuning().gs_waves_x2 / 2 / nslice)));
   kern<<<dim3(gx, nslice), threads, smem, st>>>(rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, jslice, out,
                                                 ldj, ldo);
   ++nl;
@@ -457,6 +557,11 @@ struct Lane {
   void* GtT = nullptr;
   double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
   double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr;
+  double* mwork = nullptr;   // FP64 work space of the m-side QR (FP32 paths)
+  double *C1m = nullptr, *Cgm = nullptr, *Mapplym = nullptr;   // W-side augmentation (FP32 paths)
+  void* Kw = nullptr;        // the source's moment factor in the n-side type (FP32 paths)
+  void* svdV = nullptr;      // right rotations of the truncation SVD when they do not fit shared memory
+  SstepWork sgw;             // grid-parallel S-step (2r beyond the cluster kernel's shared memory)
 };
 
 // dlra_step(n) from a given step and beam-activity pattern, captured as a CUDA graph
@@ -506,9 +611,15 @@ struct dlra_ctx {
   int* flags_dev = nullptr;
   int* schedule_dev = nullptr;
   double* dose_tmp = nullptr;
+  double* zeros = nullptr;   // n zeros
   // ray sets of the beams (for dlra_reset with retrace)
   std::vector<double*> ray_dev;
   std::vector<int> ray_count;
+  // joint mode: every beam feeds one low-rank state (held by beam 0); stacked source factors
+  bool joint = false;
+  void* joint_A = nullptr;      // n x (M n_beams), n-side type
+  double* joint_B = nullptr;    // m x (M n_beams)
+  int joint_cols = 0;
   // reverse sweep: checkpoint interval (0 = off) and its work space (AdjWork<T>*)
   int ckpt_interval = 0;
   int adj_store = 1;  // reverse sweep keeps the replayed segment's stage inputs when they fit
@@ -602,9 +713,12 @@ void moments_at(const dlra_ctx* c, int i, double E, std::vector<double>& self, s
       src[l] = C * (s[l] - corr);
     }
   } else {
+    // Fokker-Planck; transport_correction == 2: the delta-function corrected expansion (the
+    // moments shifted so that degree N+1 vanishes; Sigma_t = G_0), the self-scattering unchanged
+    const double shift = c->cfg.transport_correction == 2 ? 0.5 * xi1 * (c->N + 1.0) * (c->N + 2.0) : 0.0;
     for (int l = 0; l <= c->N; ++l) {
       self[l] = -0.5 * xi1 * l * (l + 1.0);
-      src[l] = self[l];
+      src[l] = self[l] + shift;
     }
   }
 }
@@ -691,7 +805,8 @@ struct Engine {
     rp.mode = ctx->cfg.rank_mode;
     if (adj_rank && rp.mode == DLRA_RANK_SCHEDULE) rp.mode = DLRA_RANK_ADAPTIVE;
     rp.rank = ctx->cfg.rank;
-    rp.rank_max = ctx->RB;
+    // the configured maximum (the capacity RB is rank_max rounded up to a compiled tile width)
+    rp.rank_max = (ctx->cfg.rank_max > 0 && ctx->cfg.rank_max < ctx->RB) ? ctx->cfg.rank_max : ctx->RB;
     rp.tol = ctx->cfg.trunc_tol;
     rp.nz_tol = sizeof(T) == 8 ? 1e-14 : 1e-6;
     rp.cluster_tol = sizeof(T) == 8 ? 1e-10 : 1e-5;
@@ -703,10 +818,10 @@ struct Engine {
   void svd_truncate(double* Sh, int n2, int RB, int k, int event, Beam<T>& B) {
     if (ctx->small64)
       launch_svd_truncate<double>(L->s0, Sh, n2, RB, rank_params(), k, event, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
-                                  ctx->dev_err);
+                                  ctx->dev_err, L->svdV);
     else
       launch_svd_truncate<T>(L->s0, Sh, n2, RB, rank_params(), k, event, L->Pt, L->Qt, B.S, B.dims, B.rank_log,
-                             ctx->dev_err);
+                             ctx->dev_err, L->svdV);
   }
   double drop1() const { return sizeof(T) == 8 ? 1e-12 : 3e-4; }
   double drop2() const { return sizeof(T) == 8 ? 1e-8 : 1e-3; }
@@ -734,6 +849,31 @@ struct Engine {
                          L->Mapply, &B.dims->qx, ctx->dev_err);
       ++nl;
       apply<T>(st, n, Xh, n, lg, nullptr, L->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl);
+    }
+  }
+
+  // W^ = [W, orth((I - W W^T) K)] with K (m x qcap, ld m) on the moment-side stream: the same
+  // pivoted CholeskyQR2 as augment_x (Gram and pivoted Cholesky factor in FP64, FP32 data),
+  // the count of new columns in dims->qw (FP32 paths; the FP64 path runs launch_waug)
+  void augment_w(Beam<T>& B, const T* K, int qcap) {
+    const int m = ctx->m, RB = ctx->RB;
+    cudaStream_t sm = L->s1;
+    int64_t& nl = ctx->launches;
+    T* Wh = P(L->Wh);
+    cudaMemsetAsync(Wh + (long long)RB * m, 0, sizeof(T) * (size_t)m * RB, sm);
+    cudaMemcpyAsync(Wh, B.W, sizeof(T) * (size_t)m * RB, cudaMemcpyDeviceToDevice, sm);
+    const int* rdim = &B.dims->r;
+    cudaMemsetAsync(L->C1m, 0, sizeof(double) * RB * qcap, sm);
+    gram<T>(sm, m, B.W, m, rdim, RB, qcap, FPlain<T>{K, m, nullptr, qcap}, L->C1m, RB, nl);
+    apply<T>(sm, m, B.W, m, RB, rdim, L->C1m, RB, qcap, Wh + (long long)RB * m, m, K, T(-1), T(1), nl);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int lg = RB + qcap;
+      cudaMemsetAsync(L->Cgm, 0, sizeof(double) * lg * qcap, sm);
+      gram<T>(sm, m, Wh, m, nullptr, lg, qcap, FPlain<T>{Wh + (long long)RB * m, m, nullptr, qcap}, L->Cgm, lg, nl);
+      launch_orth_factor(sm, L->Cgm, pass == 0 ? L->C1m : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
+                         L->Mapplym, &B.dims->qw, ctx->dev_err);
+      ++nl;
+      apply<T>(sm, m, Wh, m, lg, nullptr, L->Mapplym, lg, qcap, Wh + (long long)RB * m, m, nullptr, T(1), T(0), nl);
     }
   }
 
@@ -850,8 +990,12 @@ struct Engine {
     }
     // augmentation of both bases, then the Galerkin operators on them
     augment_x(B, y, RB);
-    launch_waug<T, T>(sm, B.W, m, RB, ly, m, RB, drop1(), P(L->Wh), B.dims);
-    ++nl;
+    if (sizeof(T) == 4) {
+      augment_w(B, ly, RB);
+    } else {
+      launch_waug<T, T>(sm, B.W, m, RB, ly, m, RB, drop1(), P(L->Wh), B.dims);
+      ++nl;
+    }
     T* Xh = P(L->Xh);
     T* Wh = P(L->Wh);
     cudaMemsetAsync(L->Gc, 0, sizeof(double) * nk * n2 * n2, st);
@@ -868,9 +1012,10 @@ struct Engine {
     join();
     if (ctx->small64)
       launch_sstep<double>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns,
-                           L->Sh);
+                           L->Sh, &L->sgw, ctx->dev_err);
     else
-      launch_sstep<T>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, L->Sh);
+      launch_sstep<T>(st, L->Gc, L->Ph, nk, B.S, RB, n2, ctx->sbeta + (long long)k * ctx->nsub_max * 4, ns, L->Sh,
+                      &L->sgw, ctx->dev_err);
     ++nl;
     svd_truncate(L->Sh, n2, RB, k, 0, B);
     ++nl;
@@ -888,7 +1033,7 @@ struct Engine {
     launch_scatter_solve<T>(st, L->Mg, M, ctx->coef + (long long)k * M * (N + 1), N, B.S, B.W, m, RB,
                             P(L->L1T), ctx->dev_err);
     ++nl;
-    launch_qr_lt<T>(st, P(L->L1T), m, RB, B.dims, B.W, B.S);
+    launch_qr_lt<T>(st, P(L->L1T), m, RB, B.dims, B.W, B.S, L->mwork);
     ++nl;
   }
 
@@ -904,8 +1049,14 @@ struct Engine {
     cudaStream_t st = L->s0;
     int64_t& nl = ctx->launches;
     fork();
-    launch_waug<T, double>(L->s1, B.W, m, RB, Bk, m, Ms, drop1(), P(L->Wh), B.dims);
-    ++nl;
+    if (sizeof(T) == 4) {
+      convert_kernel<T><<<nblk((long long)m * Ms, 256), 256, 0, L->s1>>>(Bk, (long long)m * Ms, P(L->Kw));
+      ++nl;
+      augment_w(B, P(L->Kw), Ms);
+    } else {
+      launch_waug<T, double>(L->s1, B.W, m, RB, Bk, m, Ms, drop1(), P(L->Wh), B.dims);
+      ++nl;
+    }
     const T* A = Ain;
     if (!A) {
       src_vec_kernel<T><<<nblk(n, 256), 256, 0, st>>>(P(ctx->wT), psi, n, Ms, P(L->Asrc));
@@ -929,6 +1080,36 @@ struct Engine {
     ++ctx->launches;
   }
 
+  // One energy step of the joint state (held by beam 0): streaming and collided scattering once,
+  // then the first-collision source of every beam that has one at this step, each beam's rank-M
+  // factor scaled by its weight and stacked into one source of rank M x (active beams)
+  void joint_step(int k) {
+    auto& bs = beams();
+    Beam<T>& J = bs[0];
+    L = &ctx->lanes[0];
+    const long long n = ctx->n;
+    const int M = ctx->M, m = ctx->m;
+    if (J.active) {
+      streaming(J, k);
+      scattering(J, k);
+    }
+    int cols = 0;
+    for (size_t b = 0; b < bs.size(); ++b) {
+      if (!bs[b].has_src[k]) continue;
+      src_vec_scaled_kernel<T><<<nblk(n, 256), 256, 0, L->s0>>>(P(ctx->wT), bs[b].psi + (long long)k * n, n, M,
+                                                                bs[b].weight, P(ctx->joint_A) + (long long)cols * n);
+      ++ctx->launches;
+      cudaMemcpyAsync(ctx->joint_B + (long long)cols * m, bs[b].Bsrc + (long long)k * M * m,
+                      sizeof(double) * (size_t)M * m, cudaMemcpyDeviceToDevice, L->s0);
+      cols += M;
+    }
+    if (cols > 0) {
+      source_with(J, k, P(ctx->joint_A), ctx->joint_B, cols, nullptr);
+      J.active = true;
+    }
+    if (J.active) dose(J);
+  }
+
   dlra_status step_all(int nsteps) {
     const int nlanes = (int)ctx->lanes.size();
     for (int s = 0; s < nsteps; ++s) {
@@ -937,7 +1118,8 @@ struct Engine {
       cudaEventRecord(ctx->ev_step, ctx->st);
       for (int l = 0; l < nlanes; ++l) cudaStreamWaitEvent(ctx->lanes[l].s0, ctx->ev_step, 0);
       auto& bs = beams();
-      for (size_t b = 0; b < bs.size(); ++b) {
+      if (ctx->joint && !bs.empty()) joint_step(k);
+      for (size_t b = 0; b < bs.size() && !ctx->joint; ++b) {
         Beam<T>& B = bs[b];
         L = &ctx->lanes[b % nlanes];
         if (ctx->ckpt_interval > 0 && k % ctx->ckpt_interval == 0)
@@ -1065,6 +1247,7 @@ dlra_status alloc_shared(dlra_ctx* ctx) {
   ALLOC(ctx->dev_err, sizeof(int));
   ALLOC(ctx->flags_dev, sizeof(int) * ctx->K);
   ALLOC(ctx->dose_tmp, sizeof(double) * n);
+  ALLOC(ctx->zeros, sizeof(double) * n);
   return DLRA_OK;
 }
 
@@ -1099,6 +1282,27 @@ dlra_status alloc_lane(dlra_ctx* ctx) {
   ALLOC(L.Qt, sizeof(double) * n2 * RB);
   ALLOC(L.Mg, sizeof(double) * M * RB * RB);
   ALLOC(L.XA, sizeof(double) * n2 * M);
+  if (sizeof(T) == 4) {
+    ALLOC(L.mwork, sizeof(double) * mside_work_doubles(m, RB));
+    ALLOC(L.C1m, sizeof(double) * RB * RB);
+    ALLOC(L.Cgm, sizeof(double) * n2 * RB);
+    ALLOC(L.Mapplym, sizeof(double) * n2 * RB);
+    ALLOC(L.Kw, sizeof(T) * (size_t)m * std::max(RB, M));
+  }
+  const size_t tsmall = ctx->small64 ? sizeof(double) : sizeof(T);   // arithmetic of the SVD and S-step
+  if (svd_needs_vwork(n2, tsmall)) ALLOC(L.svdV, tsmall * (size_t)n2 * n2);
+  if (sstep_needs_grid(nk, n2, tsmall)) {
+    const size_t ne = (size_t)n2 * n2;
+    ALLOC(L.sgw.z, tsmall * ne);
+    ALLOC(L.sgw.U, tsmall * ne * nk);
+    ALLOC(L.sgw.O, tsmall * ne * nk);
+    ALLOC(L.sgw.bar, 4 * sizeof(unsigned));
+    const int cap = sstep_grid_capacity(tsmall);
+    const int nt = (n2 + 15) / 16;
+    const int share = cap / std::max(1, ctx->max_lanes);
+    L.sgw.grid = std::max(1, std::min(nk * nt * nt, share));
+    if (cap <= 0) return fail(ctx, DLRA_ERR_CUDA, "occupancy query of the S-step kernel failed");
+  }
   return DLRA_OK;
 }
 
@@ -1262,6 +1466,9 @@ dlra_status set_materials_t(dlra_ctx* ctx, const double* w_host) {
     if (ctx->cfg.collision == DLRA_BOLTZMANN) {
       const std::vector<double>& s = ctx->s_unit[i];
       g0 = (s[0] - (ctx->cfg.transport_correction ? s[ctx->N + 1] : 0.0)) / ctx->xi_unit[i];
+    } else if (ctx->cfg.transport_correction == 2) {
+      // corrected Fokker-Planck: Sigma_t = (xi_1/2)(N+1)(N+2) = (T_w/2) rho kappa (N+1)(N+2)/2
+      g0 = 0.5 * (ctx->N + 1.0) * (ctx->N + 2.0);
     }
     ctx->tau_coef[i] = mt.density * mt.scatter_ratio * g0;
     for (long long x = 0; x < n; ++x) {
@@ -1546,9 +1753,17 @@ dlra_status dose_t(dlra_ctx* ctx, double* out, int on_device, int per_mass) {
   auto& bs = beams_of<T>(ctx);
   double* dst = on_device ? out : ctx->dose_tmp;
   if (bs.empty()) CK(cudaMemsetAsync(dst, 0, sizeof(double) * n, ctx->st));
-  for (size_t b = 0; b < bs.size(); ++b)
-    dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[b].e_c, bs[b].e_u, n, b == 0 ? 1 : 0, bs[b].weight,
-                                                         dst);
+  if (ctx->joint && !bs.empty()) {
+    // the joint state's collided deposit carries the beam weights already (they scale its
+    // sources); the uncollided deposits enter times their beam's weight
+    scale_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[0].e_c, 1.0, n, dst);
+    for (size_t b = 0; b < bs.size(); ++b)
+      dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(ctx->zeros, bs[b].e_u, n, 0, bs[b].weight, dst);
+  } else {
+    for (size_t b = 0; b < bs.size(); ++b)
+      dose_total_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(bs[b].e_c, bs[b].e_u, n, b == 0 ? 1 : 0, bs[b].weight,
+                                                           dst);
+  }
   if (per_mass) div_kernel<<<nblk(n, 256), 256, 0, ctx->st>>>(dst, ctx->rho, n);
   CK(cudaGetLastError());
   if (!on_device) {
@@ -1803,16 +2018,21 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[16] = {0};
+  double rep[20] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
-  // path, nx even)
-  double stage_ms[4];
-  for (int v = 0; v < 4; ++v) {
-    if ((v == 1 || v == 3) && sizeof(T) != 4) {
+  // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
+  // nx % 4 == 0, rank capacity >= 32)
+  double stage_ms[6];
+  for (int v = 0; v < 6; ++v) {
+    if ((v == 1 || v == 3 || v >= 4) && sizeof(T) != 4) {
       stage_ms[v] = -1.0;
       continue;
     }
     if (v == 3 && ctx->geo.nx % 2 != 0) {
+      stage_ms[v] = -1.0;
+      continue;
+    }
+    if (v >= 4 && (ctx->geo.nact != 3 || ctx->geo.nx % 4 != 0 || RB < 32 || n % 4 != 0)) {
       stage_ms[v] = -1.0;
       continue;
     }
@@ -1858,7 +2078,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   cudaFree(flush);
   Tuning best = ctx->tun;
   int sv = 0;
-  for (int v = 1; v < 4; ++v)
+  for (int v = 1; v < 6; ++v)
     if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
   best.kstage_variant = sv;
   int bi = 0;
@@ -1875,6 +2095,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   rep[9] = best.kstage_variant;
   rep[12] = stage_ms[2];
   rep[15] = stage_ms[3];
+  rep[16] = stage_ms[4];
+  rep[17] = stage_ms[5];
   rep[10] = best.gram_blocks;
   rep[11] = best.gs_waves_x2;
   ctx->tun = best;
@@ -2013,6 +2235,8 @@ dlra_status dlra_init(const dlra_config* cfg, dlra_ctx** out) {
   if (!(g.dx > 0 && g.dz > 0 && (ctx->two_d || g.dy > 0))) return fail(ctx, DLRA_ERR_ARG, "voxel sizes must be > 0");
   if (g.sh_degree < 1 || g.sh_degree > 31) return fail(ctx, DLRA_ERR_ARG, "sh_degree must be in [1, 31]");
   if (g.collision != DLRA_FOKKER_PLANCK && g.collision != DLRA_BOLTZMANN) return fail(ctx, DLRA_ERR_ARG, "bad collision");
+  if (g.transport_correction < 0 || g.transport_correction > 2)
+    return fail(ctx, DLRA_ERR_ARG, "transport_correction must be 0, 1 or 2");
   if (g.rank_mode < 0 || g.rank_mode > 2) return fail(ctx, DLRA_ERR_ARG, "bad rank_mode");
   if (g.precision != DLRA_FP64 && g.precision != DLRA_FP32_MIXED && g.precision != DLRA_FP32_SPLIT)
     return fail(ctx, DLRA_ERR_ARG, "bad precision");
@@ -2163,6 +2387,7 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval) {
   if (ctx->poisoned) return ctx->poisoned;
   if (checkpoint_interval < 0) return fail(ctx, DLRA_ERR_ARG, "checkpoint_interval must be >= 0");
   if (ctx->step != 0) return fail(ctx, DLRA_ERR_STATE, "the reverse sweep must be enabled before the first step");
+  if (ctx->joint && checkpoint_interval > 0) return fail(ctx, DLRA_ERR_STATE, "the joint state has no reverse sweep");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   if (checkpoint_interval != ctx->ckpt_interval) {
@@ -2227,6 +2452,38 @@ dlra_status dlra_add_beam(dlra_ctx* ctx, const dlra_beam* beam, int32_t* beam_id
   return ctx->fp64 ? add_beam_t<double>(ctx, beam, beam_id) : add_beam_t<float>(ctx, beam, beam_id);
 }
 
+// Work space of the joint state for nb beams: the stacked source factors (n x M nb and
+// m x M nb) and lane 0's source-projection buffer widened to M nb columns. The stacked source
+// augments the basis by up to M nb columns, which must fit the augmentation's rank capacity.
+dlra_status ensure_joint(dlra_ctx* ctx, int nb) {
+  const int cols = ctx->M * nb;
+  if (cols > ctx->RB)
+    return fail(ctx, DLRA_ERR_ARG, "joint state: %d beams x %d materials = %d source columns exceed the rank capacity %d",
+                nb, ctx->M, cols, ctx->RB);
+  if (cols <= ctx->joint_cols) return DLRA_OK;
+  CK(cudaStreamSynchronize(ctx->st));
+  const size_t tsz = ctx->fp64 ? sizeof(double) : sizeof(float);
+  dfree(ctx, ctx->joint_A);
+  dfree(ctx, ctx->joint_B);
+  dfree(ctx, ctx->lanes[0].XA);
+  ALLOC(ctx->joint_A, tsz * (size_t)ctx->n * cols);
+  ALLOC(ctx->joint_B, sizeof(double) * (size_t)ctx->m * cols);
+  ALLOC(ctx->lanes[0].XA, sizeof(double) * (size_t)ctx->n2 * cols);
+  ctx->joint_cols = cols;
+  return DLRA_OK;
+}
+
+dlra_status dlra_set_joint(dlra_ctx* ctx, int32_t enable) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (ctx->step != 0) return fail(ctx, DLRA_ERR_STATE, "the beam mode must be set before the first step");
+  if (enable && ctx->ckpt_interval > 0) return fail(ctx, DLRA_ERR_STATE, "the joint state has no reverse sweep");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->joint = enable != 0;
+  return DLRA_OK;
+}
+
 dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
@@ -2239,8 +2496,12 @@ dlra_status dlra_step(dlra_ctx* ctx, int32_t n_steps) {
     dlra_status s = ctx->fp64 ? ensure_checkpoints<double>(ctx) : ensure_checkpoints<float>(ctx);
     if (s != DLRA_OK) return s;
   }
+  if (ctx->joint) {
+    dlra_status s = ensure_joint(ctx, (int)nb);
+    if (s != DLRA_OK) return s;
+  }
   TuneScope scope(&ctx->tun);
-  if (ctx->graphs && !ctx->profiling && n_steps > 0)
+  if (ctx->graphs && !ctx->joint && !ctx->profiling && n_steps > 0)
     return ctx->fp64 ? step_graph<double>(ctx, n_steps) : step_graph<float>(ctx, n_steps);
   return ctx->fp64 ? Engine<double>{ctx}.step_all(n_steps) : Engine<float>{ctx}.step_all(n_steps);
 }
@@ -2257,7 +2518,7 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 3) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0, 1, 2 or 3");
+  if (variant < 0 || variant > 5) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 5");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;

@@ -34,16 +34,47 @@ void launch_orth_factor(cudaStream_t st, const double* G, const double* C1, int 
 
 // Truncated SVD of Sh (n2 x n2, ld n2, FP64) by one-sided Jacobi in precision T;
 // writes P, Q (n2 x RB, ld n2), S (RB x RB, ld RB), dims->r, rank_log[2*step + event].
+// vwork (n2 x n2 values of T, global memory): holds the right rotations when the two
+// n2 x n2 matrices do not fit shared memory together (FP64 at n2 = 128); required then.
 template <typename T>
 void launch_svd_truncate(cudaStream_t st, const double* Sh, int n2, int RB, RankParams rp, int step, int event,
-                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err);
+                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err,
+                         void* vwork = nullptr);
+
+// true when launch_svd_truncate<T> at this size needs vwork
+inline bool svd_needs_vwork(int n2, size_t tsize) { return 2 * (size_t)n2 * n2 * tsize > 200 * 1024; }
+
+// Work space of the grid-parallel S-step (global memory, one per lane): the stage input z
+// (n2 x n2), the products U_k = z P_k and the partial outputs O_k = G_k U_k (nk x n2 x n2 each),
+// all in the arithmetic type; three barrier words (arrivals, generation, abort), zeroed once;
+// grid = the lane's share of the co-resident blocks (cooperative launch).
+struct SstepWork {
+  void *z = nullptr, *U = nullptr, *O = nullptr;
+  unsigned* bar = nullptr;
+  int grid = 0;
+};
 
 // Galerkin S-step (Sec. 2.2, Eq. KLS) with RK4 in Horner form: Sh (n2 x n2) starts at
 // [[S, 0], [0, 0]] and is advanced by nsub sub-steps with beta[4*j + 0..3];
-// operator S -> sum_k Gh_k S Ph_k, Gh and Ph laid out [(k*n2 + b)*n2 + a].
+// operator S -> sum_k Gh_k S Ph_k, Gh and Ph laid out [(k*n2 + b)*n2 + a]. On a cluster of
+// eight blocks where its operators fit their shared memory; otherwise, with gw, on the whole
+// grid (cooperative launch, bounded barriers that set ERR_TIMEOUT in err when they run out);
+// without gw on one block.
 template <typename T>
 void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
-                  const double* beta, int nsub, double* Sh);
+                  const double* beta, int nsub, double* Sh, const SstepWork* gw = nullptr, int* err = nullptr);
+
+// doubles of global work space of the grid-parallel S-step for arithmetic type of size tsize
+inline size_t sstep_grid_bytes(int nk, int n2, size_t tsize) {
+  return (1 + 2 * (size_t)nk) * (size_t)n2 * n2 * tsize;
+}
+
+// true when the S-step of this size needs the grid-parallel kernel (the cluster kernel's
+// operators do not fit its shared memory)
+bool sstep_needs_grid(int nk, int n2, size_t tsize);
+
+// blocks of the grid-parallel S-step that fit the current device at once (0 on error)
+int sstep_grid_capacity(size_t tsize);
 
 // Implicit-Euler collided L-step (Sec. 3.3.3 step 1): per degree l solves
 // (I - sum_i coef[i*(N+1)+l] Mg_i) x = S W[p,:]^T for every moment p of degree l;
@@ -53,14 +84,26 @@ void launch_scatter_solve(cudaStream_t st, const double* Mg, int M, const double
                           const T* W, int m, int RB, T* L1T, int* err);
 
 // Householder QR of L1T (m x r): L1T = Wt R; writes Wt (m x RB, zero beyond r) and S = R^T.
+// gwork (FP32 data only): 2 m RB doubles of global work space; the QR then runs in FP64
+// arithmetic (in shared memory where the FP64 matrix and Q fit, else in gwork) and Wt is
+// rounded to FP32 at the end. nullptr: arithmetic in T, shared memory.
 template <typename T>
-void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S);
+void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S,
+                  double* gwork = nullptr);
 
 // W-side augmentation (one block): Wh = [W | orth((I - W W^T) K)], K m x qcap of type KT,
 // rank-revealing with pivoted Gram-Schmidt (drop below drop_tol ||K||_F); writes dims->qw.
+// gwork (FP32 data only): mside_work_doubles(m, RB) doubles of global work space; the
+// orthogonalisation then runs in FP64 arithmetic and the new columns are rounded to FP32.
 template <typename T, typename KT>
 void launch_waug(cudaStream_t st, const T* W, int m, int RB, const KT* K, long long ldk, int qcap, double drop_tol,
-                 T* Wh, BeamDims* dims);
+                 T* Wh, BeamDims* dims, double* gwork = nullptr);
+
+// doubles of global work space for the FP64 m-side factorisations (launch_qr_lt, launch_waug
+// with qcap <= RB)
+inline size_t mside_work_doubles(int m, int RB) {
+  return 2 * (size_t)m * RB + (size_t)RB * RB + 2 * (size_t)RB;
+}
 
 // Source S assembly: Sh (n2 x n2) = [[S, 0], [0, 0]] + h XA (B^T Wh), XA (n2 x M, ld n2),
 // B (m x M, ld m, FP64), Wh (m x n2).

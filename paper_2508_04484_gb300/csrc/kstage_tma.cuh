@@ -1,0 +1,278 @@
+// K-stage on the tensor cores with TMA halo staging (FP32 path, 3-D grids, rank capacity >= 32):
+// acc(i, :) = sum_k D_k(v)(i, :) P_k, the r x r mix of the six stencil values of every input
+// column (Sec. 3.3.2, Eq. KLS first line), as the product D[cells x N] = A[cells x K] B[K x N]
+// with K = (column c, stencil k) = c NK + k and B[K][n] = P_k[c][n].
+//
+// A CTA owns a brick of 128 TILES cells (8 x 4 TILES x 4, one TMEM lane per cell) and walks the
+// input columns in chunks of four (K = 24 per chunk) through a two-stage ring:
+//   * the producer warp loads the chunk's input values of the brick and its two-cell halo with
+//     one 4-D TMA copy (box 16 x (4 TILES + 4) x 8 x 4; the zero fill outside the grid is the
+//     vacuum ghost layer) and writes the chunk's B rows (TF32 high and low parts, K-major)
+//     from the stacked P;
+//   * 4 TILES formation warps (one thread per cell) form the cell's 24 stencil values from the
+//     staged halo, split them into TF32 high and low parts and store them K-major;
+//   * one thread of the MMA warp issues three tcgen05.mma kind::tf32 per 8-wide K slice and
+//     tile (hi*hi + hi*lo + lo*hi: FP32-accurate products, FP32 accumulation in tensor memory)
+//     and commits to the stage's free barrier.
+// The epilogue reads each cell's accumulator row from tensor memory and applies the Horner
+// update of kstage_kernel. Every wait is bounded: a wait that runs out marks the block, stops
+// the issue of new work, lets the copies and products in flight finish (bounded), frees the
+// tensor memory and sets ERR_TIMEOUT.
+#pragma once
+#include "device.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace dlra {
+
+template <int RM, int TILES>
+struct KsTma {
+  static constexpr int NACT = 3, NK = 6;
+  static constexpr int NP = ((RM + 15) / 16) * 16;                  // MMA N
+  static constexpr int TCOLS = TILES * NP <= 32 ? 32 : (TILES * NP <= 64 ? 64 : (TILES * NP <= 128 ? 128 : 256));
+  static constexpr int CC = 4;                                       // columns per chunk
+  static constexpr int KC = CC * NK;                                 // 24
+  static constexpr int TX = 8, TY = 4 * TILES, TZ = 4;               // brick
+  static constexpr int BX = 16, BY = TY + 4, BZ = TZ + 4;            // TMA box (x from x0 - 4)
+  static constexpr int HALO = BX * BY * BZ;                          // values per column
+  static constexpr int NFORM = 4 * TILES;                            // formation warps
+  static constexpr int THREADS = 32 * (NFORM + 2);                   // + producer + MMA warps
+  static constexpr int ASZ = 128 * TILES * KC;                       // floats per A part (hi or lo)
+  static constexpr int BSZ = NP * KC;                                // floats per B part
+  static constexpr int HSZ = CC * HALO;                              // floats per halo stage
+  // per stage: Ahi, Alo, Bhi, Blo, halo; 1024-byte aligned parts
+  static constexpr size_t al(size_t b) { return (b + 1023) / 1024 * 1024; }
+  static constexpr size_t OFF_AHI = 0;
+  static constexpr size_t OFF_ALO = al(ASZ * 4);
+  static constexpr size_t OFF_BHI = OFF_ALO + al(ASZ * 4);
+  static constexpr size_t OFF_BLO = OFF_BHI + al(BSZ * 4);
+  static constexpr size_t OFF_H = OFF_BLO + al(BSZ * 4);
+  static constexpr size_t STAGE = OFF_H + al(HSZ * 4);
+  static constexpr size_t SMEM = 2 * STAGE + 1024;                   // + alignment slack
+  static constexpr uint32_t HALO_BYTES = HSZ * 4;
+};
+
+template <int RM, int TILES>
+unsigned kstage_tma_grid(const Geo& g) {
+  using C = KsTma<RM, TILES>;
+  return (unsigned)(((g.nx + C::TX - 1) / C::TX) * ((g.ny + C::TY - 1) / C::TY) * ((g.nz + C::TZ - 1) / C::TZ));
+}
+
+// mode: as kstage_kernel (0 vout = rho^-1 (y + beta acc); 1 also yout = y + beta acc, vout =
+// rho^-1 yout; 2 transposed operator: vout = beta rho^-1 acc, yout = y + vout)
+template <int RM, int TILES>
+__global__ void __launch_bounds__(KsTma<RM, TILES>::THREADS) kstage_tma_kernel(
+    const __grid_constant__ CUtensorMap tmap, const float* __restrict__ y, float* __restrict__ yout,
+    float* __restrict__ vout, long long ld, const float* __restrict__ inv_rho, Geo g,
+    const float* __restrict__ Pst, const int* __restrict__ rdim, float beta, int mode, int* err) {
+  using C = KsTma<RM, TILES>;
+  constexpr int NK = C::NK, CC = C::CC, KC = C::KC, NP = C::NP, TCOLS = C::TCOLS;
+  constexpr int TX = C::TX, TY = C::TY, BX = C::BX, BY = C::BY, BZ = C::BZ, HALO = C::HALO;
+  constexpr int NFORM = C::NFORM;
+  extern __shared__ unsigned char raw_dyn[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)raw_dyn + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[2], afull_bar[2], free_bar[2], acc_bar;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int s_bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = dev_dim(rdim, RM);
+  const int nch = (r + CC - 1) / CC;
+  if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&full_bar[s], 2);        // the producer's expect_tx arrival + its arrival after B
+      tc::mbar_init(&afull_bar[s], NFORM);   // one arrival per formation warp
+      tc::mbar_init(&free_bar[s], 1);        // tcgen05.commit of the stage's products
+    }
+    tc::mbar_init(&acc_bar, 1);
+    tc::mbar_fence_init();
+    s_bad = 0;
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  const int bxn = (g.nx + TX - 1) / TX, byn = (g.ny + TY - 1) / TY;
+  const int blk = blockIdx.x;
+  const int x0 = (blk % bxn) * TX, y0 = ((blk / bxn) % byn) * TY, z0 = (blk / (bxn * byn)) * C::TZ;
+  auto stage_ptr = [&](int s, size_t off) { return reinterpret_cast<float*>(base + s * C::STAGE + off); };
+
+  if (warp == NFORM) {
+    // ---------------- producer: TMA halo + B rows of each chunk ----------------
+    int issued = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int s = ch & 1;
+      if (ch >= 2) {
+        bool ok = true;
+        if (lane == 0) ok = s_bad == 0 && tc::mbar_wait(&free_bar[s], (uint32_t)(((ch - 2) >> 1) & 1), tc::kWaitLimit);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) {
+          s_bad = 1;
+          break;
+        }
+      }
+      float* H = stage_ptr(s, C::OFF_H);
+      if (lane == 0) {
+        tc::mbar_arrive_expect_tx(&full_bar[s], C::HALO_BYTES);
+        tc::tma_load_4d(H, &tmap, x0 - 4, y0 - 2, z0 - 2, ch * CC, &full_bar[s]);
+      }
+      issued = ch + 1;
+      // B rows: B[n][K] = P_k[c][n] = Pst[(c NK + k) RM + n], zero for padded n or c >= r
+      float* Bh = stage_ptr(s, C::OFF_BHI);
+      float* Bl = stage_ptr(s, C::OFF_BLO);
+      for (int e = lane; e < NP * KC; e += 32) {
+        const int n = e / KC, K = e - n * KC;
+        const int cc = K / NK, k = K - cc * NK, c = ch * CC + cc;
+        const float pv = (n < RM && c < r) ? Pst[((long long)c * NK + k) * RM + n] : 0.f;
+        float hi, lo;
+        tc::split_tf32(pv, hi, lo);
+        const int o = tc::kmajor(n, K, NP);
+        Bh[o] = hi;
+        Bl[o] = lo;
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full_bar[s]);
+    }
+    // copies in flight must land before the block leaves: wait (bounded) for the last phase
+    // of each stage that this warp started
+    if (lane == 0) {
+      for (int ch = (issued >= 2 ? issued - 2 : 0); ch < issued; ++ch)
+        tc::mbar_wait(&full_bar[ch & 1], (uint32_t)((ch >> 1) & 1), tc::kWaitLimit);
+    }
+  } else if (warp == NFORM + 1) {
+    // ---------------- MMA issue ----------------
+    int issued = 0;
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_tf32(128, NP);
+      constexpr uint32_t aLBO = (128 / 8) * 128, bLBO = (NP / 8) * 128;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int s = ch & 1;
+        if (s_bad || !tc::mbar_wait(&afull_bar[s], (uint32_t)((ch >> 1) & 1), tc::kWaitLimit)) {
+          s_bad = 1;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t ah = tc::su32(stage_ptr(s, C::OFF_AHI)), al = tc::su32(stage_ptr(s, C::OFF_ALO));
+        const uint32_t bh = tc::su32(stage_ptr(s, C::OFF_BHI)), bl = tc::su32(stage_ptr(s, C::OFF_BLO));
+#pragma unroll
+        for (int mt = 0; mt < TILES; ++mt) {
+          const uint32_t d = tmem + mt * NP;
+          const uint32_t ao = mt * 128 * KC * 4;
+#pragma unroll
+          for (int ks = 0; ks < KC / 8; ++ks) {
+            const uint32_t ak = ao + ks * 2 * aLBO, bk = ks * 2 * bLBO;
+            const uint64_t dAh = tc::smem_desc(ah + ak, aLBO, 128), dAl = tc::smem_desc(al + ak, aLBO, 128);
+            const uint64_t dBh = tc::smem_desc(bh + bk, bLBO, 128), dBl = tc::smem_desc(bl + bk, bLBO, 128);
+            const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
+            tc::mma_tf32(d, dAh, dBh, idesc, first);
+            tc::mma_tf32(d, dAh, dBl, idesc, 1u);
+            tc::mma_tf32(d, dAl, dBh, idesc, 1u);
+          }
+        }
+        tc::mma_commit(&free_bar[s]);
+        ++issued;
+      }
+      // the accumulator is complete (or, after a failure, every issued product is done)
+      tc::mma_commit(&acc_bar);
+      if (!tc::mbar_wait(&acc_bar, 0u, tc::kWaitLimit)) s_bad = 1;
+    }
+    (void)issued;
+  } else {
+    // ---------------- formation: one cell per thread ----------------
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+    const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+    float inv2[3];
+#pragma unroll
+    for (int da = 0; da < 3; ++da) inv2[da] = (float)g.inv2d[da];
+    constexpr int SY = BX, SZ = BX * BY;
+    const int hc = (lz + 2) * SZ + (ly + 2) * SY + (lx + 4);
+    const int tile = tid >> 7, row = tid & 127;
+    const int abase = tile * 128 * KC + tc::kmajor(row, 0, 128);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int s = ch & 1;
+      if (s_bad || !tc::mbar_wait(&full_bar[s], (uint32_t)((ch >> 1) & 1), tc::kWaitLimit)) {
+        s_bad = 1;
+        break;
+      }
+      const float* H = stage_ptr(s, C::OFF_H);
+      float sv[KC];
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc) {
+        const float* hv = H + cc * HALO + hc;
+        const float v0 = hv[0];
+#pragma unroll
+        for (int da = 0; da < 3; ++da) {
+          const int st = da == 0 ? 1 : (da == 1 ? SY : SZ);
+          sv[cc * NK + 2 * da] = ok ? (-3.f * v0 + 4.f * hv[-st] - hv[-2 * st]) * inv2[da] : 0.f;
+          sv[cc * NK + 2 * da + 1] = ok ? (3.f * v0 - 4.f * hv[st] + hv[2 * st]) * inv2[da] : 0.f;
+        }
+      }
+      float* Ah = stage_ptr(s, C::OFF_AHI);
+      float* Al = stage_ptr(s, C::OFF_ALO);
+#pragma unroll
+      for (int kg = 0; kg < KC / 4; ++kg) {
+        float4 h4, l4;
+        tc::split_tf32(sv[4 * kg + 0], h4.x, l4.x);
+        tc::split_tf32(sv[4 * kg + 1], h4.y, l4.y);
+        tc::split_tf32(sv[4 * kg + 2], h4.z, l4.z);
+        tc::split_tf32(sv[4 * kg + 3], h4.w, l4.w);
+        // kmajor(row, 4 kg, 128) = kmajor(row, 0, 128) + kg * 16 * 32
+        *reinterpret_cast<float4*>(Ah + abase + kg * 512) = h4;
+        *reinterpret_cast<float4*>(Al + abase + kg * 512) = l4;
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&afull_bar[s]);
+    }
+  }
+  // every role is done issuing; the MMA thread has waited for the last products
+  __syncthreads();
+  const bool alive = s_bad == 0;
+  if (warp < NFORM) {
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+    const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+    const long long i = ((long long)iz * g.ny + iy) * g.nx + ix;
+    tc::fence_after();
+    if (alive) {
+      // warp w reads TMEM lanes 32 (w % 4) .. of accumulator w / 4: exactly its own cells
+      const float ir0 = ok ? inv_rho[i] : 0.f;
+#pragma unroll
+      for (int c0 = 0; c0 < NP; c0 += 16) {
+        float acc[16];
+        if (nch > 0) {
+          tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (warp >> 2) * NP + c0, acc);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+        }
+        if (!ok) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = c0 + j;
+          if (c >= RM) break;
+          const long long e = (long long)c * ld + i;
+          if (mode == 2) {
+            const float lam = beta * ir0 * acc[j];
+            vout[e] = lam;
+            yout[e] = y[e] + lam;
+          } else if (mode == 1) {
+            const float yn = y[e] + beta * acc[j];
+            yout[e] = yn;
+            vout[e] = ir0 * yn;
+          } else {
+            vout[e] = ir0 * (y[e] + beta * acc[j]);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (tid == 0 && !alive && err) atomicOr(err, ERR_TIMEOUT);
+  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
+}  // namespace dlra

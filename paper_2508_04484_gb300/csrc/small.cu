@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -178,10 +179,10 @@ __device__ __forceinline__ void rr_pair(int round, int i, int n, int& a, int& b)
 template <typename T>
 __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restrict__ Sh, int n2, int RB, RankParams rp, int step, int event,
                                  double* __restrict__ P, double* __restrict__ Q, double* __restrict__ S,
-                                 BeamDims* dims, int* rank_log, int* err) {
+                                 BeamDims* dims, int* rank_log, int* err, T* __restrict__ vwork) {
   extern __shared__ __align__(16) unsigned char raw[];
   T* A = reinterpret_cast<T*>(raw);
-  T* V = A + n2 * n2;
+  T* V = vwork ? vwork : A + n2 * n2;   // right rotations: shared memory, or global when both do not fit
   __shared__ double sig[128];
   __shared__ int order[128];
   __shared__ T nrm[128];   // squared column norms, updated by each rotation
@@ -372,15 +373,17 @@ __global__ void __launch_bounds__(1024) svd_trunc_kernel(const double* __restric
 
 template <typename T>
 void launch_svd_truncate(cudaStream_t st, const double* Sh, int n2, int RB, RankParams rp, int step, int event,
-                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err) {
-  size_t smem = (size_t)2 * n2 * n2 * sizeof(T);
+                         double* P, double* Q, double* S, BeamDims* dims, int* rank_log, int* err, void* vwork) {
+  const bool vg = svd_needs_vwork(n2, sizeof(T));
+  size_t smem = (size_t)(vg ? 1 : 2) * n2 * n2 * sizeof(T);
   if (smem > 48 * 1024) cudaFuncSetAttribute(svd_trunc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  svd_trunc_kernel<T><<<1, 1024, smem, st>>>(Sh, n2, RB, rp, step, event, P, Q, S, dims, rank_log, err);
+  svd_trunc_kernel<T><<<1, 1024, smem, st>>>(Sh, n2, RB, rp, step, event, P, Q, S, dims, rank_log, err,
+                                             vg ? reinterpret_cast<T*>(vwork) : nullptr);
 }
 template void launch_svd_truncate<float>(cudaStream_t, const double*, int, int, RankParams, int, int, double*, double*,
-                                         double*, BeamDims*, int*, int*);
+                                         double*, BeamDims*, int*, int*, void*);
 template void launch_svd_truncate<double>(cudaStream_t, const double*, int, int, RankParams, int, int, double*,
-                                          double*, double*, BeamDims*, int*, int*);
+                                          double*, double*, BeamDims*, int*, int*, void*);
 
 // ---------------------------------------------------------------------------
 // Galerkin S-step with RK4 in Horner form
@@ -586,10 +589,161 @@ size_t sstep_cluster_smem(int nk, int n2) {
          (size_t)n2 * w * sizeof(double) + 16;
 }
 
+// Grid-wide barrier of a cooperative launch (all blocks co-resident): bar[0] counts arrivals,
+// bar[1] is the generation, bar[2] an abort flag. A block that waits longer than about a second
+// sets ERR_TIMEOUT and the abort flag; every later barrier of any block then returns at once,
+// so the kernel finishes (with a result the host discards: the error poisons the context).
+constexpr long long kBarrierSpins = 1LL << 24;
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vb = bar;
+    if (vb[2] == 0u) {
+      const unsigned g = vb[1];
+      __threadfence();
+      if (atomicAdd(&bar[0], 1u) == gridDim.x - 1u) {
+        atomicExch(&bar[0], 0u);
+        __threadfence();
+        atomicAdd(&bar[1], 1u);
+      } else {
+        long long it = 0;
+        while (vb[1] == g && vb[2] == 0u) {
+          if (++it > kBarrierSpins) {
+            atomicExch(&bar[2], 1u);
+            atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+// The S-step over the whole grid: per RK4 stage three phases separated by grid barriers,
+// each a list of 16 x 16 output tiles spread over the blocks:
+//   A: U_k = z P_k            (nk tiles lists),
+//   B: O_k = G_k U_k          (nk tiles lists; the sum over k is left to C),
+//   C: Sh / z update with sum_k O_k (element-wise).
+// Arithmetic in T (FP64 on the FP32-split path at 2r = 128, where the operators do not fit
+// the shared memory of a cluster); operators read from global memory (L2-resident).
+constexpr int SG_TS = 16;   // output tile
+constexpr int SG_KC = 64;   // contraction chunk held in shared memory
+
+template <typename T>
+__device__ void sg_tile(int n2, const double* __restrict__ Ad, const T* __restrict__ At, long long a_ld_row,
+                        long long a_ld_col, const double* __restrict__ Bd, const T* __restrict__ Bt,
+                        long long b_ld_row, long long b_ld_col, int i0, int j0, T* __restrict__ out, T (*sa)[SG_KC + 1],
+                        T (*sb)[SG_TS + 1]) {
+  // out[(j0 + tj) * n2 + i0 + ti] = sum_q A(i0 + ti, q) B(q, j0 + tj); A(a, q) at a * a_ld_row + q * a_ld_col
+  // from Ad (FP64) or At (T), B likewise
+  const int tid = threadIdx.x, ti = tid % SG_TS, tj = tid / SG_TS;
+  T acc = T(0);
+  for (int q0 = 0; q0 < n2; q0 += SG_KC) {
+    const int kc = min(SG_KC, n2 - q0);
+    for (int e = tid; e < SG_TS * kc; e += blockDim.x) {
+      const int a = e / kc, q = e % kc, ia = i0 + a;
+      T v = T(0);
+      if (ia < n2) {
+        const long long o = ia * a_ld_row + (long long)(q0 + q) * a_ld_col;
+        v = Ad ? T(Ad[o]) : At[o];
+      }
+      sa[a][q] = v;
+    }
+    for (int e = tid; e < kc * SG_TS; e += blockDim.x) {
+      const int j = e / kc, q = e % kc, jb = j0 + j;
+      T v = T(0);
+      if (jb < n2) {
+        const long long o = (long long)(q0 + q) * b_ld_row + jb * b_ld_col;
+        v = Bd ? T(Bd[o]) : Bt[o];
+      }
+      sb[q][j] = v;
+    }
+    __syncthreads();
+    if (tj < SG_TS)
+      for (int q = 0; q < kc; ++q) acc += sa[ti][q] * sb[q][tj];
+    __syncthreads();
+  }
+  if (tj < SG_TS && i0 + ti < n2 && j0 + tj < n2) out[(long long)(j0 + tj) * n2 + i0 + ti] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sstep_grid_kernel(const double* __restrict__ Gh, const double* __restrict__ Ph,
+                                                         int nk, const double* __restrict__ S, int RB, int n2,
+                                                         const double* __restrict__ beta, int nsub,
+                                                         double* __restrict__ Sh, T* __restrict__ z,
+                                                         T* __restrict__ U, T* __restrict__ O, unsigned* bar,
+                                                         int* err) {
+  __shared__ T sa[SG_TS][SG_KC + 1];
+  __shared__ T sb[SG_KC][SG_TS + 1];
+  const long long ne = (long long)n2 * n2;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gnt = (long long)gridDim.x * blockDim.x;
+  for (long long e = gtid; e < ne; e += gnt) {
+    const int a = (int)(e % n2), c = (int)(e / n2);
+    const double y = (a < RB && c < RB) ? S[c * RB + a] : 0.0;
+    Sh[e] = y;
+    z[e] = T(y);
+  }
+  grid_barrier(bar, err);
+  const int nt = (n2 + SG_TS - 1) / SG_TS;
+  const int ntask = nk * nt * nt;
+  for (int js = 0; js < nsub; ++js) {
+    for (int s4 = 0; s4 < 4; ++s4) {
+      // A: U_k(a, j) = sum_q z(a, q) P_k(q, j);  z(a, q) at q n2 + a, P_k(q, j) at (k n2 + j) n2 + q
+      for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+        const int k = t / (nt * nt), ij = t % (nt * nt), i0 = (ij % nt) * SG_TS, j0 = (ij / nt) * SG_TS;
+        sg_tile<T>(n2, nullptr, z, 1, n2, Ph + (long long)k * ne, nullptr, 1, n2, i0, j0, U + (long long)k * ne, sa,
+                   sb);
+      }
+      grid_barrier(bar, err);
+      // B: O_k(a, j) = sum_q G_k(a, q) U_k(q, j);  G_k(a, q) at (k n2 + q) n2 + a
+      for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+        const int k = t / (nt * nt), ij = t % (nt * nt), i0 = (ij % nt) * SG_TS, j0 = (ij / nt) * SG_TS;
+        sg_tile<T>(n2, Gh + (long long)k * ne, nullptr, 1, n2, nullptr, U + (long long)k * ne, 1, n2, i0, j0,
+                   O + (long long)k * ne, sa, sb);
+      }
+      grid_barrier(bar, err);
+      // C: the Horner update
+      const double b = beta[4 * js + s4];
+      for (long long e = gtid; e < ne; e += gnt) {
+        T acc = T(0);
+        for (int k = 0; k < nk; ++k) acc += O[(long long)k * ne + e];
+        const double nv = Sh[e] + b * (double)acc;
+        if (s4 == 3) Sh[e] = nv;
+        z[e] = T(nv);
+      }
+      grid_barrier(bar, err);
+    }
+  }
+}
+
+bool sstep_needs_grid(int nk, int n2, size_t tsize) {
+  return (tsize == 4 ? sstep_cluster_smem<float>(nk, n2) : sstep_cluster_smem<double>(nk, n2)) > 200 * 1024;
+}
+
 template <typename T>
 void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, const double* S, int RB, int n2,
-                  const double* beta, int nsub, double* Sh) {
+                  const double* beta, int nsub, double* Sh, const SstepWork* gw, int* err) {
   const size_t csmem = sstep_cluster_smem<T>(nk, n2);
+  if (csmem > 200 * 1024 && gw && gw->grid > 0 && err) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gw->grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, sstep_grid_kernel<T>, Gh, Ph, nk, S, RB, n2, beta, nsub, Sh,
+                       reinterpret_cast<T*>(gw->z), reinterpret_cast<T*>(gw->U), reinterpret_cast<T*>(gw->O), gw->bar,
+                       err);
+    return;
+  }
   if (csmem <= 200 * 1024) {
     if (csmem > 48 * 1024)
       cudaFuncSetAttribute(sstep_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
@@ -626,9 +780,23 @@ void launch_sstep(cudaStream_t st, const double* Gh, const double* Ph, int nk, c
   }
 }
 template void launch_sstep<float>(cudaStream_t, const double*, const double*, int, const double*, int, int,
-                                  const double*, int, double*);
+                                  const double*, int, double*, const SstepWork*, int*);
 template void launch_sstep<double>(cudaStream_t, const double*, const double*, int, const double*, int, int,
-                                   const double*, int, double*);
+                                   const double*, int, double*, const SstepWork*, int*);
+
+// co-resident blocks of the grid-parallel S-step kernel on the current device
+int sstep_grid_capacity(size_t tsize) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = tsize == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sstep_grid_kernel<float>, 256, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sstep_grid_kernel<double>, 256, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per;
+}
 
 // ---------------------------------------------------------------------------
 // implicit-Euler collided L-step: one block per degree l
@@ -719,42 +887,46 @@ template void launch_scatter_solve<double>(cudaStream_t, const double*, int, con
 // ---------------------------------------------------------------------------
 // Householder QR of L1T (m x r): L1T = Wt R, S = R^T
 // ---------------------------------------------------------------------------
-template <typename T>
+// CT is the arithmetic type. With gwork == nullptr (CT == T) the matrix is held in shared
+// memory and Q is built in place in Wt; with gwork (2 m RB values of CT, global memory) both
+// the matrix and Q live there and Q is rounded to T at the end: the FP64 QR of FP32 data, whose
+// m x RB FP64 matrix does not fit in shared memory for m = 484.
+template <typename T, typename CT>
 __global__ void __launch_bounds__(512) qr_lt_kernel(const T* __restrict__ L1T, int m, int RB, const BeamDims* __restrict__ dims,
-                             T* __restrict__ Wt, double* __restrict__ S) {
+                             T* __restrict__ Wt, double* __restrict__ S, CT* __restrict__ gwork) {
   extern __shared__ __align__(16) unsigned char raw[];
-  T* A = reinterpret_cast<T*>(raw);   // m x RB col-major; reflectors below the diagonal
-  __shared__ T red[32];
-  __shared__ T rdiag[64], v0s[64], vn2[64];
+  CT* A = gwork ? gwork : reinterpret_cast<CT*>(raw);   // m x RB col-major; reflectors below the diagonal
+  __shared__ CT red[32];
+  __shared__ CT rdiag[64], v0s[64], vn2[64];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   int r = dims->r;
   if (r > RB) r = RB;
   if (r > m) r = m;
-  for (int e = tid; e < m * RB; e += nt) A[e] = L1T[e];
+  for (int e = tid; e < m * RB; e += nt) A[e] = CT(L1T[e]);
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    T part = 0;
+    CT part = 0;
     for (int i = j + tid; i < m; i += nt) part += A[j * m + i] * A[j * m + i];
-    T nrm2 = block_sum(part, red);
-    T x0 = A[j * m + j];
-    T nrm = sqrt(nrm2);
-    T alpha = (x0 >= T(0)) ? -nrm : nrm;
-    T v0 = x0 - alpha;
-    T vnorm2 = nrm2 - x0 * x0 + v0 * v0;
+    CT nrm2 = block_sum(part, red);
+    CT x0 = A[j * m + j];
+    CT nrm = sqrt(nrm2);
+    CT alpha = (x0 >= CT(0)) ? -nrm : nrm;
+    CT v0 = x0 - alpha;
+    CT vnorm2 = nrm2 - x0 * x0 + v0 * v0;
     __syncthreads();
     if (tid == 0) {
-      rdiag[j] = (nrm2 > T(0)) ? alpha : T(0);
+      rdiag[j] = (nrm2 > CT(0)) ? alpha : CT(0);
       v0s[j] = v0;
-      vn2[j] = (nrm2 > T(0)) ? vnorm2 : T(0);
+      vn2[j] = (nrm2 > CT(0)) ? vnorm2 : CT(0);
       A[j * m + j] = v0;  // reflector v = (v0, A[j+1:, j])
     }
     __syncthreads();
-    if (vn2[j] > T(0)) {
+    if (vn2[j] > CT(0)) {
       for (int c = j + 1 + wid; c < r; c += nw) {
-        T d = 0;
+        CT d = 0;
         for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * A[c * m + i];
         d = warp_sum(d);
-        T f = T(2) * d / vn2[j];
+        CT f = CT(2) * d / vn2[j];
         for (int i = j + lane; i < m; i += 32) A[c * m + i] -= f * A[j * m + i];
       }
     }
@@ -771,47 +943,72 @@ __global__ void __launch_bounds__(512) qr_lt_kernel(const T* __restrict__ L1T, i
     S[e] = v;
   }
   __syncthreads();
-  // Q = H_0 ... H_{r-1} applied to the first r identity columns; build in place
-  // using a second buffer region: reuse Wt (global) as workspace
+  // Q = H_0 ... H_{r-1} applied to the first r identity columns
+  CT* Q;
+  if constexpr (std::is_same<CT, T>::value) Q = gwork ? gwork + (size_t)m * RB : Wt;
+  else Q = (gwork ? gwork : A) + (size_t)m * RB;   // FP64 Q after the matrix (global or shared)
   for (int e = tid; e < m * RB; e += nt) {
     int i = e % m, c = e / m;
-    Wt[e] = (c < r && i == c) ? T(1) : T(0);
+    Q[e] = (c < r && i == c) ? CT(1) : CT(0);
   }
   __syncthreads();
   for (int j = r - 1; j >= 0; --j) {
-    if (!(vn2[j] > T(0))) continue;
+    if (!(vn2[j] > CT(0))) continue;
     for (int c = j + wid; c < r; c += nw) {
-      T d = 0;
-      for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * Wt[(long long)c * m + i];
+      CT d = 0;
+      for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * Q[(long long)c * m + i];
       d = warp_sum(d);
-      T f = T(2) * d / vn2[j];
-      for (int i = j + lane; i < m; i += 32) Wt[(long long)c * m + i] -= f * A[j * m + i];
+      CT f = CT(2) * d / vn2[j];
+      for (int i = j + lane; i < m; i += 32) Q[(long long)c * m + i] -= f * A[j * m + i];
     }
     __syncthreads();
   }
+  if (!std::is_same<CT, T>::value || gwork)
+    for (int e = tid; e < m * RB; e += nt) Wt[e] = T(Q[e]);
 }
 
 template <typename T>
-void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S) {
+void launch_qr_lt(cudaStream_t st, const T* L1T, int m, int RB, const BeamDims* dims, T* Wt, double* S,
+                  double* gwork) {
+  if (gwork && sizeof(T) == 4) {
+    // FP64 arithmetic: the matrix and Q in shared memory when both fit, else in gwork
+    const size_t smem64 = (size_t)2 * m * RB * sizeof(double);
+    if (smem64 <= 200 * 1024) {
+      cudaFuncSetAttribute(qr_lt_kernel<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+      qr_lt_kernel<T, double><<<1, 512, smem64, st>>>(L1T, m, RB, dims, Wt, S, nullptr);
+    } else {
+      qr_lt_kernel<T, double><<<1, 512, 0, st>>>(L1T, m, RB, dims, Wt, S, gwork);
+    }
+    return;
+  }
   size_t smem = (size_t)m * RB * sizeof(T);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(qr_lt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  qr_lt_kernel<T><<<1, 512, smem, st>>>(L1T, m, RB, dims, Wt, S);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(qr_lt_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  qr_lt_kernel<T, T><<<1, 512, smem, st>>>(L1T, m, RB, dims, Wt, S, nullptr);
 }
-template void launch_qr_lt<float>(cudaStream_t, const float*, int, int, const BeamDims*, float*, double*);
-template void launch_qr_lt<double>(cudaStream_t, const double*, int, int, const BeamDims*, double*, double*);
+template void launch_qr_lt<float>(cudaStream_t, const float*, int, int, const BeamDims*, float*, double*, double*);
+template void launch_qr_lt<double>(cudaStream_t, const double*, int, int, const BeamDims*, double*, double*, double*);
 
 // ---------------------------------------------------------------------------
 // W-side augmentation: pivoted Gram-Schmidt with re-orthogonalisation
 // ---------------------------------------------------------------------------
-template <typename T, typename KT>
+// CT is the arithmetic type. With gwork == nullptr (CT == T) the residuals R and projections G
+// are in shared memory and the accepted directions are written in place into Wh; with gwork
+// (global memory, waug_work_size values of CT) R, G and the accepted directions U live there
+// and U is rounded to T at the end (the FP64 orthogonalisation of FP32 data).
+template <typename T, typename KT, typename CT>
 __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int m, int RB, const KT* __restrict__ K, long long ldk, int qcap,
-                            double drop_tol, T* __restrict__ Wh, BeamDims* dims) {
+                            double drop_tol, T* __restrict__ Wh, BeamDims* dims, CT* __restrict__ gwork) {
   extern __shared__ __align__(16) unsigned char raw[];
-  T* R = reinterpret_cast<T*>(raw);   // m x qcap
-  T* G = R + (size_t)m * qcap;        // RB x qcap projections W^T R; then the r + q projections of u
-  T* U = Wh + (long long)RB * m;      // accepted new directions, written in place
-  __shared__ T red[32];
-  __shared__ T cn[64];
+  CT* R = gwork ? gwork : reinterpret_cast<CT*>(raw);   // m x qcap
+  CT* G = R + (size_t)m * qcap;        // RB x qcap projections W^T R; then the r + q projections of u
+  CT* U;                               // accepted new directions
+  if constexpr (std::is_same<CT, T>::value)
+    U = gwork ? G + (size_t)max(RB * qcap, RB + qcap) : Wh + (long long)RB * m;
+  else
+    U = G + (size_t)max(RB * qcap, RB + qcap);
+  __shared__ CT red[32];
+  __shared__ CT cn[64];
   __shared__ int used[64];
   __shared__ int s_best;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -820,32 +1017,32 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
     int i = e % m, c = e / m;
     Wh[e] = (c < RB) ? W[(long long)c * m + i] : T(0);
   }
-  T part = 0;
+  CT part = 0;
   for (int e = tid; e < m * qcap; e += nt) {
     int i = e % m, c = e / m;
-    T v = T(K[(long long)c * ldk + i]);
+    CT v = CT(K[(long long)c * ldk + i]);
     R[e] = v;
     part += v * v;
   }
   for (int c = tid; c < qcap; c += nt) used[c] = 0;
-  const T scale2 = block_sum(part, red);
-  const T thr = T(drop_tol * drop_tol) * scale2;
+  const CT scale2 = block_sum(part, red);
+  const CT thr = CT(drop_tol * drop_tol) * scale2;
   // two passes of R -= W (W^T R) (classical Gram-Schmidt twice): all r qcap projections at
   // once over the warps, then one fused update per element
   for (int pass = 0; pass < 2; ++pass) {
     __syncthreads();
     for (int e = wid; e < r * qcap; e += nw) {
       const int a = e % r, c = e / r;
-      T d = 0;
-      for (int i = lane; i < m; i += 32) d += W[(long long)a * m + i] * R[c * m + i];
+      CT d = 0;
+      for (int i = lane; i < m; i += 32) d += CT(W[(long long)a * m + i]) * R[c * m + i];
       d = warp_sum(d);
       if (lane == 0) G[c * RB + a] = d;
     }
     __syncthreads();
     for (int e = tid; e < m * qcap; e += nt) {
       const int i = e % m, c = e / m;
-      T v = R[e];
-      for (int a = 0; a < r; ++a) v -= G[c * RB + a] * W[(long long)a * m + i];
+      CT v = R[e];
+      for (int a = 0; a < r; ++a) v -= G[c * RB + a] * CT(W[(long long)a * m + i]);
       R[e] = v;
     }
   }
@@ -853,15 +1050,15 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
   int q = 0;
   for (int it = 0; it < qcap; ++it) {
     for (int c = wid; c < qcap; c += nw) {
-      T d = 0;
+      CT d = 0;
       for (int i = lane; i < m; i += 32) d += R[c * m + i] * R[c * m + i];
       d = warp_sum(d);
-      if (lane == 0) cn[c] = used[c] ? T(-1) : d;
+      if (lane == 0) cn[c] = used[c] ? CT(-1) : d;
     }
     __syncthreads();
     if (tid == 0) {
       int b = -1;
-      T bv = thr;
+      CT bv = thr;
       for (int c = 0; c < qcap; ++c)
         if (cn[c] > bv) { bv = cn[c]; b = c; }
       s_best = b;
@@ -873,33 +1070,35 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
     // u = R[:, b] re-orthogonalised against W and the accepted directions (one classical
     // Gram-Schmidt pass over all warps, R being orthogonal to both up to round-off already),
     // normalised
-    T* u = U + q * m;
+    CT* u = U + q * m;
     for (int i = tid; i < m; i += nt) u[i] = R[b * m + i];
     __syncthreads();
     for (int a = wid; a < r + q; a += nw) {
-      const T* v = a < r ? W + (long long)a * m : U + (long long)(a - r) * m;
-      T d = 0;
-      for (int i = lane; i < m; i += 32) d += v[i] * u[i];
+      CT d = 0;
+      if (a < r)
+        for (int i = lane; i < m; i += 32) d += CT(W[(long long)a * m + i]) * u[i];
+      else
+        for (int i = lane; i < m; i += 32) d += U[(long long)(a - r) * m + i] * u[i];
       d = warp_sum(d);
       if (lane == 0) G[a] = d;
     }
     __syncthreads();
-    T part2 = 0;
+    CT part2 = 0;
     for (int i = tid; i < m; i += nt) {
-      T x = u[i];
-      for (int a = 0; a < r; ++a) x -= G[a] * W[(long long)a * m + i];
+      CT x = u[i];
+      for (int a = 0; a < r; ++a) x -= G[a] * CT(W[(long long)a * m + i]);
       for (int a = 0; a < q; ++a) x -= G[r + a] * U[(long long)a * m + i];
       u[i] = x;
       part2 += x * x;
     }
-    const T n2 = block_sum(part2, red);
-    const T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
+    const CT n2 = block_sum(part2, red);
+    const CT inv = n2 > CT(0) ? CT(1) / sqrt(n2) : CT(0);
     for (int i = tid; i < m; i += nt) u[i] *= inv;
     __syncthreads();
     // remove u from the remaining columns
     for (int c = wid; c < qcap; c += nw) {
       if (used[c]) continue;
-      T d = 0;
+      CT d = 0;
       for (int i = lane; i < m; i += 32) d += u[i] * R[c * m + i];
       d = warp_sum(d);
       for (int i = lane; i < m; i += 32) R[c * m + i] -= d * u[i];
@@ -907,24 +1106,30 @@ __global__ void __launch_bounds__(512) waug_kernel(const T* __restrict__ W, int 
     ++q;
     __syncthreads();
   }
+  if (gwork)
+    for (int e = tid; e < m * q; e += nt) Wh[(long long)RB * m + e] = T(U[e]);
   if (tid == 0) dims->qw = q;
 }
 
 template <typename T, typename KT>
 void launch_waug(cudaStream_t st, const T* W, int m, int RB, const KT* K, long long ldk, int qcap, double drop_tol,
-                 T* Wh, BeamDims* dims) {
+                 T* Wh, BeamDims* dims, double* gwork) {
+  if (gwork && sizeof(T) == 4) {
+    waug_kernel<T, KT, double><<<1, 512, 0, st>>>(W, m, RB, K, ldk, qcap, drop_tol, Wh, dims, gwork);
+    return;
+  }
   // R (m x qcap) and the projections (RB x qcap; >= RB + qcap for those of one direction)
   const size_t smem = ((size_t)m * qcap + (size_t)std::max(RB * qcap, RB + qcap)) * sizeof(T);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(waug_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  waug_kernel<T, KT><<<1, 512, smem, st>>>(W, m, RB, K, ldk, qcap, drop_tol, Wh, dims);
+    cudaFuncSetAttribute(waug_kernel<T, KT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  waug_kernel<T, KT, T><<<1, 512, smem, st>>>(W, m, RB, K, ldk, qcap, drop_tol, Wh, dims, nullptr);
 }
 template void launch_waug<float, float>(cudaStream_t, const float*, int, int, const float*, long long, int, double,
-                                        float*, BeamDims*);
+                                        float*, BeamDims*, double*);
 template void launch_waug<float, double>(cudaStream_t, const float*, int, int, const double*, long long, int, double,
-                                         float*, BeamDims*);
+                                         float*, BeamDims*, double*);
 template void launch_waug<double, double>(cudaStream_t, const double*, int, int, const double*, long long, int,
-                                          double, double*, BeamDims*);
+                                          double, double*, BeamDims*, double*);
 
 // ---------------------------------------------------------------------------
 // source S assembly

@@ -120,6 +120,7 @@ SIGNATURES = {
     "dlra_kernel_stats": ([_P, _DP, C.POINTER(C.c_int64)], C.c_int),
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
+    "dlra_set_joint": ([_P, C.c_int32], C.c_int),
     "dlra_stencil_gram": ([C.POINTER(dlra_stencil_gram_args)], C.c_int),
     "dlra_straggling_tables": ([C.POINTER(dlra_straggling_args), _DP, _DP, _DP, _DP], C.c_int),
     "dlra_straggling_trace": ([C.POINTER(dlra_straggling_trace_args)], C.c_int),
@@ -354,13 +355,14 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(16)
+    rep = np.zeros(20)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
                 stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), stencil_gram_tc_ms=rep[13],
-                stage_pair_ms=rep[15],
-                stage_variant=("per-cell FMA", "tensor cores", "brick FMA", "cell pairs")[int(rep[9])],
+                stage_pair_ms=rep[15], stage_tma128_ms=rep[16], stage_tma256_ms=rep[17],
+                stage_variant=("per-cell FMA", "tensor cores", "brick FMA", "cell pairs", "TMA tensor cores 128",
+                               "TMA tensor cores 256")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
                 stencil_gram_kernel=("FMA", "tensor cores")[int(rep[14])])
 
@@ -379,6 +381,10 @@ def dlra_set_tensor_cores(ctx, enable=True):
 
 def dlra_set_graphs(ctx, enable=True):
     _check(ctx, load().dlra_set_graphs(ctx, int(bool(enable))))
+
+
+def dlra_set_joint(ctx, enable=True):
+    _check(ctx, load().dlra_set_joint(ctx, 1 if enable else 0))
 
 
 def dlra_set_adjoint_store(ctx, keep=True):
@@ -592,7 +598,8 @@ class Solver:
         return dlra_autotune(self.ctx)
 
     def set_stage_kernel(self, variant):
-        """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA, 3 cell pairs (FP32, nx even)."""
+        """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA, 3 cell pairs (FP32, nx even),
+        4 / 5 TMA-staged tensor cores with 128- / 256-cell bricks (FP32, 3-D, nx % 4 == 0, rank capacity >= 32)."""
         dlra_set_stage_kernel(self.ctx, variant)
 
     def set_stencil_gram_kernel(self, variant):
@@ -602,6 +609,10 @@ class Solver:
     def set_tensor_cores(self, enable=True):
         """Run the streaming stage on the tcgen05 tensor cores (FP32-mixed path)."""
         dlra_set_tensor_cores(self.ctx, enable)
+
+    def set_joint(self, enable=True):
+        """All beams share one low-rank state (call before the first step)."""
+        dlra_set_joint(self.ctx, enable)
 
     def set_graphs(self, enable=True):
         """Capture each dlra_step call as a CUDA graph and replay it on repeated solves."""

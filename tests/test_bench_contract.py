@@ -41,18 +41,33 @@ def test_stage_kernel_markers_delimit_each_kernel(bench):
 
 def test_traffic_record_matches_the_current_sources(bench):
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
-    d = json.load(open(path))["kernels"]
     names = {n: v for v, (n, _, _) in bench.STAGE_KERNELS.items()}
-    for name, rec in d.items():
-        assert name in names
-        assert rec["dram_bytes_per_launch"] == rec["dram_read"] + rec["dram_write"]
-        assert "ncu" in rec["capture"] and "--clock-control none" in rec["capture"]
-        # the committed figure is reported only while the kernel's text is unchanged
-        traffic, note = bench._stage_traffic(names[name])
-        if rec["source_sha256"] == bench.stage_source_sha256(names[name]):
-            assert traffic == rec["dram_bytes_per_launch"]
-        else:
-            assert traffic is None and note == "kernel changed since the capture"
+    for workload, wrec in json.load(open(path))["workloads"].items():
+        assert workload in bench.WORKLOADS
+        for name, rec in wrec["kernels"].items():
+            assert name in names
+            assert rec["dram_bytes_per_launch"] == rec["dram_read"] + rec["dram_write"]
+            assert "ncu" in rec["capture"] and "--clock-control none" in rec["capture"]
+            # the committed figure is reported only while the kernel's text is unchanged
+            traffic, note = bench._stage_traffic(names[name], workload)
+            if rec["source_sha256"] == bench.stage_source_sha256(names[name]):
+                assert traffic == rec["dram_bytes_per_launch"]
+            else:
+                assert traffic is None and note == "kernel changed since the capture"
+
+
+def test_stage_work_counts(bench):
+    # (5r + 1) words and 2 nk r^2 + 6 nk r flops per cell and launch, four launches per sub-step,
+    # none before the first source step (rank 0)
+    import numpy as np
+    cfg = dict(nx=4, ny=3, nz=2, dy=0.2, precision=1)
+    r_start = np.array([0, 2, 3])
+    nsub = [5, 2, 1]
+    nl, byts, flops = bench.stage_work(cfg, r_start, nsub)
+    assert nl == 4 * 2 + 4 * 1
+    assert byts == 24 * 4 * (8 * 11 + 4 * 16)
+    assert flops == 24 * (8 * (2 * 6 * 4 + 6 * 6 * 2) + 4 * (2 * 6 * 9 + 6 * 6 * 3))
+    assert bench._start_ranks(np.array([[-1, 2], [3, 3], [4, -1]])).tolist() == [0, 2, 3]
 
 
 def test_stage_names_cover_the_autotuner_report(bench):

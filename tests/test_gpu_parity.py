@@ -224,3 +224,27 @@ def test_state_errors():
         s.step(cfg["n_steps"] + 1)
     assert e.value.status == 2
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(WL.FP64, 1e-5), (WL.FP32_MIXED, 1e-3)])
+def test_fokker_planck_delta_correction_matches_oracle(precision, tol):
+    # the delta-function corrected Fokker-Planck moments (transport_correction = 2): the
+    # uncollided beam is removed at Sigma_t = (xi_1/2)(N+1)(N+2) and feeds a first-collision
+    # source with a non-zero l = 0 moment; ray trace and whole solve against the oracle
+    cfg, mats, w, beams = _slab(collision=WL.FP, precision=precision)
+    cfg["transport_correction"] = 2
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    assert np.abs(src[0][0]).max() > 0
+    dose, res = oracle_dlra(prob, src, OP.FIXED, rank=6)
+    s = gpu_solver(cfg, mats, w, beams, schedule=res[0]["ranks"], precision=precision)
+    for k in (0, 3, 7):
+        psi, e_u = s.source(k)
+        assert rel_l2(psi, src[0][0][k]) < 1e-8
+    assert rel_l2(e_u, src[0][1]) < 1e-8
+    dg = s.run()
+    assert np.array_equal(s.rank_log(), res[0]["ranks"])
+    err = rel_l2(dg, dose)
+    print(f"Fokker-Planck with the delta-function correction, precision {precision}: dose error {err:.2e}")
+    assert err < tol
+    s.close()

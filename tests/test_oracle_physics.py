@@ -56,3 +56,54 @@ def test_material_tables_fp_and_boltzmann():
     assert abs(bz.sigma_t(1, E) - (sig[0] - sig[N + 1])) < 1e-15 * sig[0]
     # sigma_0 - sigma_1 equals xi_1 of the material
     assert abs((sig[0] - sig[1]) / bz.xi1(1, E) - 1) < 1e-12
+
+
+def _exponential_kernel_etc_moments(eps, N):
+    """Unit-xi_1 moments of the kernel exp(-(1 - mu)/eps) under the extended transport
+    correction, by Gauss-Legendre quadrature in x = 1 - mu on graded panels (independent of the
+    oracle's kernels): returns (sigma_l - sigma_{N+1}) / xi_1 for l = 0..N."""
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    edges = [0.0]
+    h = eps / 8
+    while edges[-1] + h < 2.0:
+        edges.append(edges[-1] + h)
+        h *= 1.5
+    edges.append(2.0)
+    mu, w = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        mu.append(1.0 - (0.5 * (b - a) * xg + 0.5 * (b + a)))
+        w.append(0.5 * (b - a) * wg)
+    mu, w = np.concatenate(mu), np.concatenate(w)
+    k = np.exp(-(1.0 - mu) / eps)
+    sig = np.array([2 * np.pi * np.sum(w * np.polynomial.legendre.legval(mu, np.eye(N + 2)[l]) * k)
+                    for l in range(N + 2)])
+    xi = 2 * np.pi * np.sum(w * (1.0 - mu) * k)
+    return (sig[: N + 1] - sig[N + 1]) / xi
+
+
+def test_delta_corrected_fokker_planck_is_the_forward_peaked_limit():
+    # the corrected Fokker-Planck moments (xi/2)[(N+1)(N+2) - l(l+1)] are what the extended
+    # transport correction gives for a Boltzmann kernel in the forward-peaked limit at fixed xi_1:
+    # the difference falls linearly with the kernel width
+    N = 5
+    l = np.arange(N + 1)
+    limit = 0.5 * ((N + 1) * (N + 2) - l * (l + 1))
+    errs = [np.abs(_exponential_kernel_etc_moments(eps, N) - limit).max() / limit.max()
+            for eps in (1e-2, 1e-3, 1e-4)]
+    assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8 and errs[2] < 1e-3
+    # the oracle's tables with the correction flag (2)
+    mats = [ph.Material(1.0), ph.Material(1.85, 0.9, 1.35, 1.5e-3)]
+    fp = ph.PhysicsTables(mats, N, ph.FOKKER_PLANCK, 2, 1.77, 0.0022, 1.72e-4)
+    fp0 = ph.PhysicsTables(mats, N, ph.FOKKER_PLANCK, 0, 1.77, 0.0022, 1.72e-4)
+    E = 70.0
+    xi = fp.xi1(1, E)
+    G, St = fp.moments(1, E)
+    assert np.abs(G / xi - _exponential_kernel_etc_moments(1e-5, N)).max() < 1e-4 * limit.max()
+    assert St == G[0] and abs(fp.sigma_t(1, E) - G[0]) < 1e-15 * G[0]
+    # the degree N+1 moment of the corrected expansion vanishes; self-scattering is unchanged
+    assert abs(0.5 * xi * ((N + 1) * (N + 2) - (N + 1) * (N + 2))) == 0.0
+    assert np.allclose(fp.self_scatter(1, E), fp0.self_scatter(1, E), rtol=1e-13, atol=0)
+    # the value 1 keeps the uncorrected Fokker-Planck moments (the extended transport correction
+    # applies to the Boltzmann moments only)
+    fp1 = ph.PhysicsTables(mats, N, ph.FOKKER_PLANCK, 1, 1.77, 0.0022, 1.72e-4)
+    assert np.array_equal(fp1.moments(1, E)[0], fp0.moments(1, E)[0]) and fp1.sigma_t(1, E) == 0.0

@@ -93,3 +93,24 @@ def test_layered_slab_matches_ode():
         sol = solve_ivp(rhs, (k * dz, (k + 1) * dz), y, rtol=1e-12, atol=1e-14, method="DOP853")
         y = sol.y[:, -1]
     assert abs(res.exit_energy / (y[0] * y[1]) - 1) < 1e-8
+
+
+def test_fokker_planck_delta_correction_attenuates_the_beam():
+    # with the delta-function corrected Fokker-Planck moments the uncollided beam is removed at
+    # Sigma_t = (xi_1/2)(N+1)(N+2) = (T_w/4)(N+1)(N+2): in homogeneous water along a normal ray
+    # N(s) = exp(-int Sigma_t ds) in closed form, and the energy balance closes
+    cfg = dict(nx=4, ny=1, nz=30, dx=0.5, dy=0.0, dz=0.2, N=3, collision="fp", transport_correction=2,
+               e_max=100.0, e_min=1.0, n_steps=40, t100=5e-3)
+    prob = P.Problem(cfg, [dict(density=1.0)], np.ones((1, 120)))
+    beam = dict(energy=100.0, pos=[1.1, 0, 0], dir=[0, 0, 1], spot_sigma=0.0)
+    res = RT.trace(prob, beam, nq=16)
+    p, alpha, N = 1.77, 0.0022, 3
+    c = 0.25 * (N + 1) * (N + 2) * 5e-3 * 1e4 * p * alpha      # Sigma_t / S_w = c E^(p-3)
+    R0 = alpha * 100.0 ** p
+    L = 30 * 0.2
+    E_L = ((R0 - L) / alpha) ** (1 / p)
+    N_L = math.exp(-c * (100.0 ** (p - 2) - E_L ** (p - 2)) / (p - 2))
+    assert abs(res.removed_particles - (1 - N_L)) < 1e-10
+    tot = res.e_u.sum() * prob.volume + res.removed_energy + res.exit_energy + res.cutoff_energy
+    assert abs(tot / res.input_energy - 1) < 1e-12
+    assert res.removed_energy > 0.1 * res.input_energy
