@@ -326,28 +326,43 @@ bool stage_tensor_map(CUtensorMap* m, const float* vin, const Geo& g, long long 
 
 // the TMA-staged tensor-core stage at a rank capacity and brick (FP32, 3-D, rcap >= 32);
 // false when the grid or the buffers do not meet its layout rules (the caller falls back)
+// bytes of the B-operand images of the TMA-staged stage at rank capacity RB (the larger brick)
+size_t kstage_tma_bimg_bytes(int RB) {
+  switch (RB) {
+    case 32: return (size_t)KsTma<32, 2>::NCH * KsTma<32, 2>::BIMG_BYTES;
+    case 40: return (size_t)KsTma<40, 2>::NCH * KsTma<40, 2>::BIMG_BYTES;
+    case 48: return (size_t)KsTma<48, 2>::NCH * KsTma<48, 2>::BIMG_BYTES;
+    case 64: return (size_t)KsTma<64, 2>::NCH * KsTma<64, 2>::BIMG_BYTES;
+    default: return 0;
+  }
+}
+
 template <int RM, int TILES>
 bool kstage_tma_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
-                       int* err) {
+                       int* err, void* bimg) {
   using C = KsTma<RM, TILES>;
+  if (!bimg) return false;
   CUtensorMap m;
   if (!stage_tensor_map(&m, vin, g, n, RM, C::BY)) return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  kstage_tma_bimg_kernel<RM, TILES><<<nblk((long long)C::NCH * C::NP * C::KC, 256), 256, 0, st>>>(Pst, rdim, img);
   cudaFuncSetAttribute(kstage_tma_kernel<RM, TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   kstage_tma_kernel<RM, TILES><<<kstage_tma_grid<RM, TILES>(g), C::THREADS, C::SMEM, st>>>(
-      m, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err);
+      m, y, yout, vout, n, inv_rho, g, img, rdim, beta, last, err);
   return true;
 }
 
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
-                   const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant) {
+                   const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant,
+                   void* bimg) {
   if constexpr (sizeof(T) == 4 && NACT == 3 && RM >= 32) {
     if (variant == 4 || variant == 5) {
       const bool done = variant == 4 ? kstage_tma_launch<RM, 1>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
-                                                                beta, last, err)
+                                                                beta, last, err, bimg)
                                      : kstage_tma_launch<RM, 2>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
-                                                                beta, last, err);
+                                                                beta, last, err, bimg);
       if (done) return;
       variant = 0;
     }
@@ -393,10 +408,10 @@ void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, 
 template <typename T, int NACT>
 void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n,
                      const T* inv_rho, const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err,
-                     int tc) {
+                     int tc, void* bimg) {
   switch (RB) {
 #define KS_CASE(R) \
-  case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc); break;
+  case R: kstage_launch<T, R, NACT>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc, bimg); break;
     KS_CASE(4) KS_CASE(8) KS_CASE(12) KS_CASE(16) KS_CASE(20) KS_CASE(24) KS_CASE(32)
     KS_CASE(40) KS_CASE(48) KS_CASE(64)
 #undef KS_CASE
@@ -408,9 +423,10 @@ void kstage_dispatch(int RB, cudaStream_t st, const T* vin, const T* y, T* yout,
 template <typename T>
 void kstage(int RB, cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
             const Geo& g, const T* Pst, const int* rdim, T beta, int last, int64_t& nl, int* err = nullptr,
-            int tc = 0) {
-  if (g.nact == 3) kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
-  else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc);
+            int tc = 0, void* bimg = nullptr) {
+  if (g.nact == 3)
+    kstage_dispatch<T, 3>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc, bimg);
+  else kstage_dispatch<T, 2>(RB, st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, tc, bimg);
   ++nl;
 }
 
@@ -561,6 +577,7 @@ struct Lane {
   double *C1m = nullptr, *Cgm = nullptr, *Mapplym = nullptr;   // W-side augmentation (FP32 paths)
   void* Kw = nullptr;        // the source's moment factor in the n-side type (FP32 paths)
   void* svdV = nullptr;      // right rotations of the truncation SVD when they do not fit shared memory
+  void* Bimg = nullptr;      // B-operand images of the TMA-staged tensor-core stage
   SstepWork sgw;             // grid-parallel S-step (2r beyond the cluster kernel's shared memory)
 };
 
@@ -970,14 +987,14 @@ struct Engine {
           const int sf = 3 - s2;
           const T* vin = s2 == 0 ? va : capq(4 * j + sf + 1);
           kstage<T>(RB, st, vin, y, y, capq(4 * j + sf), n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tun.kstage_variant);
+                    T(beta[sf]), 2, nl, ctx->dev_err, ctx->tun.kstage_variant, L->Bimg);
         } else if (cap) {
           T* vout = s2 < 3 ? capq(4 * j + s2 + 1) : (j + 1 < ns ? capq(4 * (j + 1)) : vb);
           kstage<T>(RB, st, capq(4 * j + s2), y, y, vout, n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant, L->Bimg);
         } else {
           kstage<T>(RB, st, vins[s2], y, y, vouts[s2], n, P(ctx->inv_rho), ctx->geo, P(L->Pst), rdim,
-                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant);
+                    T(beta[s2]), s2 == 3 ? 1 : 0, nl, ctx->dev_err, ctx->tun.kstage_variant, L->Bimg);
         }
         prof_end(ctx, st);
         double lbeta[4];
@@ -1289,6 +1306,8 @@ dlra_status alloc_lane(dlra_ctx* ctx) {
     ALLOC(L.Mapplym, sizeof(double) * n2 * RB);
     ALLOC(L.Kw, sizeof(T) * (size_t)m * std::max(RB, M));
   }
+  if (sizeof(T) == 4 && ctx->geo.nact == 3 && kstage_tma_bimg_bytes(RB) > 0)
+    ALLOC(L.Bimg, kstage_tma_bimg_bytes(RB));
   const size_t tsmall = ctx->small64 ? sizeof(double) : sizeof(T);   // arithmetic of the SVD and S-step
   if (svd_needs_vwork(n2, tsmall)) ALLOC(L.svdV, tsmall * (size_t)n2 * n2);
   if (sstep_needs_grid(nk, n2, tsmall)) {
@@ -2038,7 +2057,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
     }
     stage_ms[v] = time_cold_ms([&] {
       kstage<T>(RB, st, E.P(L.Kb[1]), E.P(L.Kb[0]), E.P(L.Kb[0]), E.P(L.Kb[2]), n, E.P(ctx->inv_rho), ctx->geo,
-                E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v);
+                E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v, L.Bimg);
     });
   }
   rep[0] = stage_ms[0];

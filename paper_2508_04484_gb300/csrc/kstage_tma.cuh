@@ -7,8 +7,8 @@
 // input columns in chunks of four (K = 24 per chunk) through a two-stage ring:
 //   * the producer warp loads the chunk's input values of the brick and its two-cell halo with
 //     one 4-D TMA copy (box 16 x (4 TILES + 4) x 8 x 4; the zero fill outside the grid is the
-//     vacuum ghost layer) and writes the chunk's B rows (TF32 high and low parts, K-major)
-//     from the stacked P;
+//     vacuum ghost layer) and the chunk's B rows (TF32 high and low parts, K-major, prepared
+//     once per launch by kstage_tma_bimg_kernel) with one bulk copy;
 //   * 4 TILES formation warps (one thread per cell) form the cell's 24 stencil values from the
 //     staged halo, split them into TF32 high and low parts and store them K-major;
 //   * one thread of the MMA warp issues three tcgen05.mma kind::tf32 per 8-wide K slice and
@@ -50,7 +50,36 @@ struct KsTma {
   static constexpr size_t STAGE = OFF_H + al(HSZ * 4);
   static constexpr size_t SMEM = 2 * STAGE + 1024;                   // + alignment slack
   static constexpr uint32_t HALO_BYTES = HSZ * 4;
+  // B of one chunk as laid out in shared memory (hi part, then lo part): the image one bulk
+  // copy loads
+  static constexpr uint32_t BIMG_BYTES = (uint32_t)(OFF_H - OFF_BHI);
+  static constexpr int NCH = RM / CC;                                // chunks at full capacity
 };
+
+// The B operand of every chunk, split into TF32 high and low parts and laid out K-major as the
+// stage kernel keeps it in shared memory: image[ch] = [B_hi | B_lo], B[n][K] = P_k[c][n] with
+// K = cc NK + k, c = ch CC + cc (zero for n >= RM or c >= r). Built once per launch from the
+// stacked P (rows (c NK + k), RM columns).
+template <int RM, int TILES>
+__global__ void __launch_bounds__(256) kstage_tma_bimg_kernel(const float* __restrict__ Pst,
+                                                              const int* __restrict__ rdim, float* __restrict__ img) {
+  using C = KsTma<RM, TILES>;
+  constexpr int NK = C::NK, CC = C::CC, KC = C::KC, NP = C::NP;
+  const int r = dev_dim(rdim, RM);
+  const int per = NP * KC;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= C::NCH * per) return;
+  const int ch = e / per, q = e - ch * per;
+  const int n = q / KC, K = q - n * KC;
+  const int cc = K / NK, k = K - cc * NK, c = ch * CC + cc;
+  const float pv = (n < RM && c < r) ? Pst[((long long)c * NK + k) * RM + n] : 0.f;
+  float hi, lo;
+  tc::split_tf32(pv, hi, lo);
+  float* base = img + (size_t)ch * (C::BIMG_BYTES / 4);
+  const int o = tc::kmajor(n, K, NP);
+  base[o] = hi;
+  base[(C::OFF_BLO - C::OFF_BHI) / 4 + o] = lo;
+}
 
 template <int RM, int TILES>
 unsigned kstage_tma_grid(const Geo& g) {
@@ -64,10 +93,10 @@ template <int RM, int TILES>
 __global__ void __launch_bounds__(KsTma<RM, TILES>::THREADS) kstage_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, const float* __restrict__ y, float* __restrict__ yout,
     float* __restrict__ vout, long long ld, const float* __restrict__ inv_rho, Geo g,
-    const float* __restrict__ Pst, const int* __restrict__ rdim, float beta, int mode, int* err) {
+    const float* __restrict__ Bimg, const int* __restrict__ rdim, float beta, int mode, int* err) {
   using C = KsTma<RM, TILES>;
   constexpr int NK = C::NK, CC = C::CC, KC = C::KC, NP = C::NP, TCOLS = C::TCOLS;
-  constexpr int TX = C::TX, TY = C::TY, BX = C::BX, BY = C::BY, BZ = C::BZ, HALO = C::HALO;
+  constexpr int TX = C::TX, TY = C::TY, BX = C::BX, BY = C::BY, HALO = C::HALO;
   constexpr int NFORM = C::NFORM;
   extern __shared__ unsigned char raw_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)raw_dyn + 1023) & ~(uintptr_t)1023);
@@ -80,7 +109,7 @@ __global__ void __launch_bounds__(KsTma<RM, TILES>::THREADS) kstage_tma_kernel(
   if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      tc::mbar_init(&full_bar[s], 2);        // the producer's expect_tx arrival + its arrival after B
+      tc::mbar_init(&full_bar[s], 1);        // the producer's expect_tx arrival (halo and B copies)
       tc::mbar_init(&afull_bar[s], NFORM);   // one arrival per formation warp
       tc::mbar_init(&free_bar[s], 1);        // tcgen05.commit of the stage's products
     }
@@ -111,28 +140,12 @@ __global__ void __launch_bounds__(KsTma<RM, TILES>::THREADS) kstage_tma_kernel(
           break;
         }
       }
-      float* H = stage_ptr(s, C::OFF_H);
       if (lane == 0) {
-        tc::mbar_arrive_expect_tx(&full_bar[s], C::HALO_BYTES);
-        tc::tma_load_4d(H, &tmap, x0 - 4, y0 - 2, z0 - 2, ch * CC, &full_bar[s]);
+        tc::mbar_arrive_expect_tx(&full_bar[s], C::HALO_BYTES + C::BIMG_BYTES);
+        tc::tma_load_4d(stage_ptr(s, C::OFF_H), &tmap, x0 - 4, y0 - 2, z0 - 2, ch * CC, &full_bar[s]);
+        tc::bulk_load(stage_ptr(s, C::OFF_BHI), Bimg + (size_t)ch * (C::BIMG_BYTES / 4), C::BIMG_BYTES, &full_bar[s]);
       }
       issued = ch + 1;
-      // B rows: B[n][K] = P_k[c][n] = Pst[(c NK + k) RM + n], zero for padded n or c >= r
-      float* Bh = stage_ptr(s, C::OFF_BHI);
-      float* Bl = stage_ptr(s, C::OFF_BLO);
-      for (int e = lane; e < NP * KC; e += 32) {
-        const int n = e / KC, K = e - n * KC;
-        const int cc = K / NK, k = K - cc * NK, c = ch * CC + cc;
-        const float pv = (n < RM && c < r) ? Pst[((long long)c * NK + k) * RM + n] : 0.f;
-        float hi, lo;
-        tc::split_tf32(pv, hi, lo);
-        const int o = tc::kmajor(n, K, NP);
-        Bh[o] = hi;
-        Bl[o] = lo;
-      }
-      tc::fence_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&full_bar[s]);
     }
     // copies in flight must land before the block leaves: wait (bounded) for the last phase
     // of each stage that this warp started

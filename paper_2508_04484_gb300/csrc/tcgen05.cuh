@@ -116,6 +116,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0,
       : "memory");
 }
 
+// bulk copy of `bytes` contiguous bytes from global to shared memory (both 16-byte aligned,
+// bytes a multiple of 16); completion counted on the barrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
 constexpr int kWaitLimit = 1 << 26;
 
 }  // namespace tc
