@@ -58,9 +58,11 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-second", action="store_true", help="skip the 64^3 water line")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched-against-plain comparison on the 64^3 eight-beam phantom")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
-    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3, 4, 5], default=None,
+    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3, 4, 5, 6, 7], default=None,
                    help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs, "
                         "4 / 5 TMA-staged tensor cores, 128 / 256-cell bricks), set after the autotuner")
     p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1], default=None,
@@ -90,9 +92,11 @@ STAGE_KERNELS = {
         "// Cell bricks of the staged streaming stage"),
     4: ("kstage_tma_kernel", None, None),
     5: ("kstage_tma_kernel", None, None),
+    6: ("kstage_tmap_kernel", None, None),
+    7: ("kstage_tmaa_kernel", None, None),
 }
 STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
-               "TMA tensor cores 256": 5}
+               "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7}
 
 
 def stage_source_sha256(variant):
@@ -293,18 +297,18 @@ def cpu_baseline(name, edge=16, k0=60, reps=2, one_core=True):
     return out
 
 
-def _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=False):
-    """Mean device time (ms) of one whole solve with the given number of lanes (graphs: the
-    energy steps replayed from a CUDA graph captured on the first, untimed solve)."""
+def _solve_dose(cfg, mats, w, beams, K, lanes, graphs):
+    """Device time (ms) of one whole solve after a warm-up solve, and its dose."""
     import torch
     from paper_2508_04484_gb300 import dlra as D
     stream = torch.cuda.Stream()
     s = D.Solver(dict(cfg, max_concurrent_beams=lanes), mats, w, beams, stream=stream.cuda_stream)
+    s.autotune()
+    s.set_graphs(graphs)
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     dose = torch.zeros(n, dtype=torch.float64, device="cuda")
-    s.set_graphs(graphs)
-    times = []
-    for i in range(reps + 1):
+    ms = 0.0
+    for i in range(2):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -313,23 +317,40 @@ def _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=False):
         s.dose(out=dose)
         e1.record(stream)
         e1.synchronize()
-        if i > 0:
-            times.append(e0.elapsed_time(e1))
+        ms = e0.elapsed_time(e1)
     s.close()
-    return float(np.mean(times))
+    return ms, dose.cpu().numpy()
 
 
-def _plain_vs_batched(cfg, mats, w, beams, K, args):
-    """The same multi-beam solve with one beam after the other (one lane) and with the
-    beams advanced concurrently (one lane per beam)."""
-    reps = max(1, min(args.steps, 3))
+def _plain_vs_batched(cfg, mats, w, beams, K, args=None, with_direct=False):
+    """The same multi-beam solve with one beam after the other (one lane, direct launches) and
+    with the beams advanced concurrently (one lane per beam, energy steps replayed from a CUDA
+    graph); one warm-up solve each, then one timed solve; the doses must agree."""
     lanes = min(len(beams), 32)
-    plain = _solve_ms(cfg, mats, w, beams, K, 1, reps)
-    direct = _solve_ms(cfg, mats, w, beams, K, lanes, reps)
-    graph = _solve_ms(cfg, mats, w, beams, K, lanes, reps, graphs=True)
-    return {"plain_ms_per_solve": plain, "batched_ms_per_solve": graph, "speedup": plain / graph,
-            "batched_direct_launch_ms_per_solve": direct, "beams": len(beams), "lanes": lanes,
-            "batched": "one lane (work space + stream pair) per beam, energy steps replayed from a CUDA graph"}
+    plain, d_plain = _solve_dose(cfg, mats, w, beams, K, 1, False)
+    graph, d_graph = _solve_dose(cfg, mats, w, beams, K, lanes, True)
+    out = {"plain_ms_per_solve": plain, "batched_ms_per_solve": graph, "speedup": plain / graph,
+           "beams": len(beams), "lanes": lanes, "energy_steps": K,
+           "dose_rel_diff": float(np.linalg.norm(d_graph - d_plain) / np.linalg.norm(d_plain)),
+           "batched": "one lane (work space + stream pair) per beam, energy steps replayed from a CUDA graph",
+           "plain": "one beam after the other, direct launches"}
+    if with_direct:
+        out["batched_direct_launch_ms_per_solve"], _ = _solve_dose(cfg, mats, w, beams, K, lanes, False)
+    return out
+
+
+def _batched_line(name="phantom_64cube_8beams"):
+    """Batched against plain per-beam solves of a multi-beam workload (the 64^3 eight-beam
+    phantom with beam weights U(0.5, 1.5)), with the batched solve's energy steps per second."""
+    cfg, mats, w, beams = _workload(name)
+    K = cfg["n_steps"]
+    r = _plain_vs_batched(cfg, mats, w, beams, K)
+    r["workload"] = name
+    r["config"] = _config_block(name, cfg, beams, K)
+    r["value"] = K / (r["batched_ms_per_solve"] / 1000.0)
+    r["unit"] = UNIT
+    r["beam_energy_steps_per_s"] = r["value"] * len(beams)
+    return r
 
 
 def _config_block(name, cfg, beams, K):
@@ -434,6 +455,8 @@ def main():
     vs_plain = None
     if len(beams) > 1 and ws == 1:
         vs_plain = _plain_vs_batched(cfg, mats, w, beams, K, args)
+    elif ws == 1 and not args.no_batched and name == WORKLOAD:
+        vs_plain = _batched_line()
     stream = torch.cuda.Stream(device=dev)
     # several ranks and several beams: each rank solves its share of the plan (beams are
     # independent) and the deposits are summed at the end of every solve; otherwise every rank
@@ -557,7 +580,21 @@ def main():
               "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
               "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
               "counts": "per cell and launch (5r + 1) words and 2 nk r^2 + 6 nk r flops at the step's rank"}
-    if frac_alu >= frac_hbm:
+    if variant in (1, 4, 5, 6, 7):
+        # the r x r mix on the tensor cores (kind::tf32, three products per FP32-accurate product):
+        # the dense TF32 peak from the measured sustained bf16 GEMM rate x the nominal TF32/bf16 ratio
+        bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+        tf32_peak = bf16 * 1.1 / 2.25
+        frac_tc = tfs / tf32_peak
+        if frac_tc >= frac_hbm:
+            roof = dict({"bound": "tensor", "achieved": tfs, "peak": tf32_peak, "unit": "TFLOP/s", "frac": frac_tc,
+                         "peak_source": f"{src} sustained bf16 {bf16} TFLOP/s x nominal tf32/bf16 1.1/2.25",
+                         "achieved_gbs": gbs, "hbm_frac": frac_hbm, "fp32_fma_frac": frac_alu}, **common)
+        else:
+            roof = dict({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                         "peak_source": f"{src} hbm_gbs", "achieved_tflops": tfs, "tensor_frac": frac_tc,
+                         "tensor_peak_tflops": tf32_peak, "fp32_fma_frac": frac_alu}, **common)
+    elif frac_alu >= frac_hbm:
         roof = dict({"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz} MHz ({src} clock)",
                      "achieved_gbs": gbs, "hbm_frac": frac_hbm}, **common)

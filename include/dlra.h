@@ -234,8 +234,8 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * stencil-Gram grids, the chosen stage variant (0 .. 5 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
- * the TMA-staged tensor-core stages with 128- and 256-cell bricks, two zeros (-1 where not
- * applicable). */
+ * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
+ * of its form with A in tensor memory (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -245,8 +245,12 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * 4 / 5 the r x r mix on the tensor cores (tcgen05.mma kind::tf32 with high/low TF32 splits,
  * FP32 accuracy) with each chunk of four input columns of a 128- / 256-cell brick and its
  * two-cell halo staged by one TMA copy (FP32 path, 3-D, nx and the cell count multiples of 4,
- * rank capacity >= 32; else variant 0). Same results up to rounding; dlra_autotune picks among
- * them. */
+ * rank capacity >= 32; else variant 0), 6 the 128-cell form as one persistent block per SM
+ * that streams its bricks' chunks through a four-deep TMA ring and drains one brick's TMEM
+ * accumulator while the next brick accumulates in a second one, 7 the 128-cell form with the
+ * A operand (the stencil values) written to tensor memory (tcgen05.st) and read from there by
+ * the products, leaving shared memory to the halo and B. Same results up to rounding;
+ * dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):
@@ -425,6 +429,14 @@ typedef struct {
  * (dlra_last_error(NULL)); a failed host-to-device copy returns DLRA_ERR_CUDA before the
  * launch. */
 dlra_status dlra_straggling_trace(const dlra_straggling_trace_args* args);
+
+/* enable = 1: the uncollided fluence and deposit of every beam come from the energy-DG tracer
+ * with straggling (Sec. 3.2; the computation of dlra_straggling_trace: n_elem P2 elements in
+ * energy, Crank-Nicolson steps of at most h_max cm, straggling = 0 for its CSDA limit) instead
+ * of the CSDA ray tracer, for the beams added afterwards and at every dlra_reset with a retrace
+ * (call dlra_reset(ctx, 1) to re-trace beams added before). Synchronises each trace. The
+ * reverse sweep is not available with this source (DLRA_ERR_STATE). */
+dlra_status dlra_set_straggling(dlra_ctx* ctx, int32_t enable, int32_t n_elem, double h_max, int32_t straggling);
 
 /* enable = 1: the beams of this context share one low-rank state (the paper's multi-beam
  * solve, Sec. 4.3), instead of one state per beam. Each energy step streams and scatters

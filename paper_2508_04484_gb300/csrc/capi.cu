@@ -212,7 +212,8 @@ struct Tuning {
   int gram_blocks = 1216;     // target number of blocks of the Gram reductions (x the 2-D tile grid)
   int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x SMs blocks
   int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA,
-                              // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks
+                              // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks,
+                              // 6 its persistent form, 7 with the A operand in tensor memory
   int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
 };
@@ -353,11 +354,57 @@ bool kstage_tma_launch(cudaStream_t st, const float* vin, const float* y, float*
   return true;
 }
 
+// the persistent TMA-staged tensor-core stage: one CTA per SM over the 128-cell bricks
+template <int RM>
+bool kstage_tmap_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                        int* err, void* bimg) {
+  using C = KsTmaP<RM>;
+  using B1 = KsTma<RM, 1>;
+  if (!bimg) return false;
+  CUtensorMap m;
+  if (!stage_tensor_map(&m, vin, g, n, RM, B1::BY)) return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  kstage_tma_bimg_kernel<RM, 1><<<nblk((long long)B1::NCH * B1::NP * B1::KC, 256), 256, 0, st>>>(Pst, rdim, img);
+  cudaFuncSetAttribute(kstage_tmap_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  const unsigned bricks = kstage_tma_grid<RM, 1>(g);
+  const unsigned grid = std::min<unsigned>(bricks, (unsigned)device_sms());
+  kstage_tmap_kernel<RM><<<grid, C::THREADS, C::SMEM, st>>>(m, y, yout, vout, n, inv_rho, g, img, rdim, beta, last,
+                                                             err);
+  return true;
+}
+
+// the TMA-staged stage with its A operand in tensor memory (128-cell bricks)
+template <int RM>
+bool kstage_tmaa_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                        int* err, void* bimg) {
+  using C = KsTmaA<RM>;
+  using B1 = KsTma<RM, 1>;
+  if (!bimg) return false;
+  CUtensorMap m;
+  if (!stage_tensor_map(&m, vin, g, n, RM, B1::BY)) return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  kstage_tma_bimg_kernel<RM, 1><<<nblk((long long)B1::NCH * B1::NP * B1::KC, 256), 256, 0, st>>>(Pst, rdim, img);
+  cudaFuncSetAttribute(kstage_tmaa_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  kstage_tmaa_kernel<RM><<<kstage_tma_grid<RM, 1>(g), C::THREADS, C::SMEM, st>>>(m, y, yout, vout, n, inv_rho, g, img,
+                                                                                rdim, beta, last, err);
+  return true;
+}
+
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
                    const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant,
                    void* bimg) {
   if constexpr (sizeof(T) == 4 && NACT == 3 && RM >= 32) {
+    if (variant == 7) {
+      if (kstage_tmaa_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
+      variant = 0;
+    }
+    if (variant == 6) {
+      if (kstage_tmap_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
+      variant = 0;
+    }
     if (variant == 4 || variant == 5) {
       const bool done = variant == 4 ? kstage_tma_launch<RM, 1>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim,
                                                                 beta, last, err, bimg)
@@ -532,6 +579,7 @@ struct Beam {
   int first_src = -1;         // first energy step with a first-collision source
   double weight = 1.0;        // beam weight: the beam's deposit enters the dose times weight
   double dir[3] = {0, 0, 1};
+  dlra_beam params{};         // as added (the straggling tracer re-traces from these)
   bool active = false;
   std::vector<Snap<T>> ckpt;  // states at the start of steps 0, I, 2I, ... (adjoint enabled)
 };
@@ -632,6 +680,11 @@ struct dlra_ctx {
   // ray sets of the beams (for dlra_reset with retrace)
   std::vector<double*> ray_dev;
   std::vector<int> ray_count;
+  // uncollided source from the energy-DG straggling tracer (dlra_set_straggling) instead of
+  // the CSDA tracer
+  bool strag = false;
+  int strag_elems = 128, strag_on = 1;
+  double strag_hmax = 0.01;
   // joint mode: every beam feeds one low-rank state (held by beam 0); stacked source factors
   bool joint = false;
   void* joint_A = nullptr;      // n x (M n_beams), n-side type
@@ -1586,6 +1639,34 @@ dlra_status upload_bsrc(dlra_ctx* ctx, Beam<T>& B) {
   return DLRA_OK;
 }
 
+// The beam's uncollided fluence per energy bin and deposit from the energy-DG straggling tracer
+// (Sec. 3.2; dlra_straggling_trace), in place of the CSDA tracer's
+dlra_status straggling_source(dlra_ctx* ctx, const dlra_beam& b, double* psi, double* e_u) {
+  const dlra_config& c = ctx->cfg;
+  dlra_straggling_trace_args a{};
+  a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
+  a.dx = c.dx; a.dy = c.dy; a.dz = c.dz;
+  a.e_min = c.e_min; a.e_max = c.e_max;
+  a.n_bins = ctx->K;
+  a.n_elem = ctx->strag_elems;
+  a.h_max = ctx->strag_hmax;
+  a.bk_p = c.bk_p; a.bk_alpha = c.bk_alpha; a.t100 = c.t100;
+  a.straggling = ctx->strag_on;
+  a.energy = b.energy; a.energy_sigma = b.energy_sigma; a.spot_sigma = b.spot_sigma;
+  for (int q = 0; q < 3; ++q) {
+    a.pos[q] = b.pos[q];
+    a.dir[q] = b.dir[q];
+  }
+  a.f_cell = ctx->f_cell;
+  a.tau_cell = ctx->tau_cell;
+  a.psi = psi;
+  a.e_u = e_u;
+  a.cuda_stream = ctx->st;
+  dlra_status s = dlra_straggling_trace(&a);
+  if (s != DLRA_OK) return fail(ctx, s, "straggling trace: %s", dlra_last_error(nullptr));
+  return DLRA_OK;
+}
+
 template <typename T>
 dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
   const long long n = ctx->n;
@@ -1671,6 +1752,7 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
   }
   Beam<T> B;
   B.weight = b->weight;
+  B.params = *b;
   for (int a = 0; a < 3; ++a) B.dir[a] = d[a];
   ALLOC(B.X, sizeof(T) * n * RB);
   ALLOC(B.W, sizeof(T) * (size_t)m * RB);
@@ -1691,7 +1773,12 @@ dlra_status add_beam_t(dlra_ctx* ctx, const dlra_beam* b, int32_t* id) {
   RayGeo g = ray_geo(ctx);
   ctx->ray_dev.push_back(rays_dev);
   ctx->ray_count.push_back(nray);
-  launch_raytrace(ctx->st, rays_dev, nray, g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+  if (ctx->strag) {
+    dlra_status ss = straggling_source(ctx, *b, B.psi, B.e_u);
+    if (ss != DLRA_OK) return ss;
+  } else {
+    launch_raytrace(ctx->st, rays_dev, nray, g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+  }
   ++ctx->launches;
   int* flags = nullptr;
   ALLOC(flags, sizeof(int) * K);
@@ -1809,10 +1896,15 @@ dlra_status reset_t(dlra_ctx* ctx, int retrace, bool flags_changed = false) {
     if (retrace) {
       CK(cudaMemsetAsync(B.psi, 0, sizeof(double) * (size_t)ctx->K * n, ctx->st));
       CK(cudaMemsetAsync(B.e_u, 0, sizeof(double) * n, ctx->st));
-      launch_raytrace(ctx->st, ctx->ray_dev[b], ctx->ray_count[b], g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+      if (ctx->strag) {
+        dlra_status ss = straggling_source(ctx, B.params, B.psi, B.e_u);
+        if (ss != DLRA_OK) return ss;
+      } else {
+        launch_raytrace(ctx->st, ctx->ray_dev[b], ctx->ray_count[b], g, ctx->f_cell, ctx->tau_cell, B.psi, B.e_u);
+      }
       ++ctx->launches;
-      if (flags_changed) {
-        // the mixture changed: the bins the beam reaches may have changed too
+      if (flags_changed || ctx->strag) {
+        // the mixture or the tracer changed: the bins the beam reaches may have changed too
         CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(int) * ctx->K, ctx->st));
         bin_flags_kernel<<<dim3(std::min<unsigned>(nblk(n, 256), 64), ctx->K), 256, 0, ctx->st>>>(B.psi, n, ctx->K,
                                                                                                   ctx->flags_dev);
@@ -2041,8 +2133,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
   // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
   // nx % 4 == 0, rank capacity >= 32)
-  double stage_ms[6];
-  for (int v = 0; v < 6; ++v) {
+  double stage_ms[8];
+  for (int v = 0; v < 8; ++v) {
     if ((v == 1 || v == 3 || v >= 4) && sizeof(T) != 4) {
       stage_ms[v] = -1.0;
       continue;
@@ -2097,7 +2189,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   cudaFree(flush);
   Tuning best = ctx->tun;
   int sv = 0;
-  for (int v = 1; v < 6; ++v)
+  for (int v = 1; v < 8; ++v)
     if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
   best.kstage_variant = sv;
   int bi = 0;
@@ -2116,6 +2208,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   rep[15] = stage_ms[3];
   rep[16] = stage_ms[4];
   rep[17] = stage_ms[5];
+  rep[18] = stage_ms[6];
+  rep[19] = stage_ms[7];
   rep[10] = best.gram_blocks;
   rep[11] = best.gs_waves_x2;
   ctx->tun = best;
@@ -2407,6 +2501,8 @@ dlra_status dlra_enable_adjoint(dlra_ctx* ctx, int32_t checkpoint_interval) {
   if (checkpoint_interval < 0) return fail(ctx, DLRA_ERR_ARG, "checkpoint_interval must be >= 0");
   if (ctx->step != 0) return fail(ctx, DLRA_ERR_STATE, "the reverse sweep must be enabled before the first step");
   if (ctx->joint && checkpoint_interval > 0) return fail(ctx, DLRA_ERR_STATE, "the joint state has no reverse sweep");
+  if (ctx->strag && checkpoint_interval > 0)
+    return fail(ctx, DLRA_ERR_STATE, "the reverse sweep differentiates the CSDA tracer only");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   if (checkpoint_interval != ctx->ckpt_interval) {
@@ -2492,6 +2588,22 @@ dlra_status ensure_joint(dlra_ctx* ctx, int nb) {
   return DLRA_OK;
 }
 
+dlra_status dlra_set_straggling(dlra_ctx* ctx, int32_t enable, int32_t n_elem, double h_max, int32_t straggling) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (enable && (n_elem < 1 || n_elem > 4096 || !(h_max > 0.0)))
+    return fail(ctx, DLRA_ERR_ARG, "straggling source: n_elem in [1, 4096] and h_max > 0 required");
+  if (enable && ctx->ckpt_interval > 0)
+    return fail(ctx, DLRA_ERR_STATE, "the reverse sweep differentiates the CSDA tracer only");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->strag = enable != 0;
+  ctx->strag_elems = n_elem;
+  ctx->strag_hmax = h_max;
+  ctx->strag_on = straggling != 0;
+  return DLRA_OK;
+}
+
 dlra_status dlra_set_joint(dlra_ctx* ctx, int32_t enable) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
@@ -2537,7 +2649,7 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 5) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 5");
+  if (variant < 0 || variant > 7) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 7");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;

@@ -121,6 +121,7 @@ SIGNATURES = {
     "dlra_kstep": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_kstep_noalloc": ([C.POINTER(dlra_kstep_args)], C.c_int),
     "dlra_set_joint": ([_P, C.c_int32], C.c_int),
+    "dlra_set_straggling": ([_P, C.c_int32, C.c_int32, C.c_double, C.c_int32], C.c_int),
     "dlra_stencil_gram": ([C.POINTER(dlra_stencil_gram_args)], C.c_int),
     "dlra_straggling_tables": ([C.POINTER(dlra_straggling_args), _DP, _DP, _DP, _DP], C.c_int),
     "dlra_straggling_trace": ([C.POINTER(dlra_straggling_trace_args)], C.c_int),
@@ -361,8 +362,10 @@ def dlra_autotune(ctx):
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
                 stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), stencil_gram_tc_ms=rep[13],
                 stage_pair_ms=rep[15], stage_tma128_ms=rep[16], stage_tma256_ms=rep[17],
+                stage_tma_persistent_ms=rep[18], stage_tma_tmem_a_ms=rep[19],
                 stage_variant=("per-cell FMA", "tensor cores", "brick FMA", "cell pairs", "TMA tensor cores 128",
-                               "TMA tensor cores 256")[int(rep[9])],
+                               "TMA tensor cores 256", "TMA tensor cores persistent",
+                               "TMA tensor cores A in TMEM")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
                 stencil_gram_kernel=("FMA", "tensor cores")[int(rep[14])])
 
@@ -381,6 +384,10 @@ def dlra_set_tensor_cores(ctx, enable=True):
 
 def dlra_set_graphs(ctx, enable=True):
     _check(ctx, load().dlra_set_graphs(ctx, int(bool(enable))))
+
+
+def dlra_set_straggling(ctx, enable=True, n_elem=128, h_max=0.01, straggling=True):
+    _check(ctx, load().dlra_set_straggling(ctx, 1 if enable else 0, int(n_elem), float(h_max), 1 if straggling else 0))
 
 
 def dlra_set_joint(ctx, enable=True):
@@ -599,7 +606,9 @@ class Solver:
 
     def set_stage_kernel(self, variant):
         """0 per-cell FMA, 1 tensor cores (FP32 path), 2 brick-staged FMA, 3 cell pairs (FP32, nx even),
-        4 / 5 TMA-staged tensor cores with 128- / 256-cell bricks (FP32, 3-D, nx % 4 == 0, rank capacity >= 32)."""
+        4 / 5 TMA-staged tensor cores with 128- / 256-cell bricks (FP32, 3-D, nx % 4 == 0, rank capacity >= 32),
+        6 the same as one persistent CTA per SM with overlapped epilogue, 7 128-cell bricks with the A operand
+        in tensor memory."""
         dlra_set_stage_kernel(self.ctx, variant)
 
     def set_stencil_gram_kernel(self, variant):
@@ -609,6 +618,13 @@ class Solver:
     def set_tensor_cores(self, enable=True):
         """Run the streaming stage on the tcgen05 tensor cores (FP32-mixed path)."""
         dlra_set_tensor_cores(self.ctx, enable)
+
+    def set_straggling(self, enable=True, n_elem=128, h_max=0.01, straggling=True):
+        """Uncollided source from the energy-DG straggling tracer (Sec. 3.2); re-traces the
+        beams already added."""
+        dlra_set_straggling(self.ctx, enable, n_elem, h_max, straggling)
+        if self.beam_ids:
+            self.reset(retrace=True)
 
     def set_joint(self, enable=True):
         """All beams share one low-rank state (call before the first step)."""

@@ -65,3 +65,32 @@ def test_straggling_trace_matches_oracle(case, beam_kw, straggling):
     ref = ST.trace_straggling(prob, beam, n_elem=G, h_max=0.01, straggling=straggling)
     assert rel_l2(e_u.cpu().numpy(), ref.e_u) < 1e-12
     assert rel_l2(psi.cpu().numpy(), ref.psi) < 1e-12
+
+
+@pytest.mark.parametrize("straggling", [False, True])
+def test_solver_with_straggling_source_matches_oracle(straggling):
+    # the solver's uncollided source from the energy-DG tracer (dlra_set_straggling) against the
+    # oracle's low-rank solve driven by its own energy-DG tracer (oracle/straggling.py)
+    from oracle import dlra as ODL
+    from paper_2508_04484_gb300 import dlra as D
+    cfg = WL.base_config(nx=16, ny=1, nz=20, dx=0.2, dy=0.0, dz=0.2, N=3, collision=WL.BOLTZMANN,
+                         rank_mode=WL.FIXED, rank=4, rank_max=8, e_max=66.0, e_min=30.0, n_steps=8,
+                         precision=WL.FP64, t100=2e-2)
+    mats, w = WL.homogeneous(cfg)
+    beam = WL.pencil_beam(60.0, (1.3, 0.0, 0.0), (0.2, 0.0, 1.0), spot_sigma=0.1, energy_sigma=1.5)
+    prob = OP.Problem(cfg, mats, w)
+    tr = ST.trace_straggling(prob, beam, n_elem=128, h_max=0.01, straggling=straggling)
+    d = np.asarray(beam["dir"]) / np.linalg.norm(beam["dir"])
+    ref = ODL.solve(prob, [(tr.psi, tr.e_u, d)], ODL.RankControl(mode=OP.FIXED, rank=4))
+    c = dict(cfg, rank_mode=WL.SCHEDULE, rank_schedule=ref["ranks"])
+    s = D.Solver(c, mats, w, [beam])
+    s.set_straggling(True, n_elem=128, h_max=0.01, straggling=straggling)
+    psi0, e_u = s.source(2)
+    assert rel_l2(psi0, tr.psi[2]) < 1e-12
+    assert rel_l2(e_u, tr.e_u) < 1e-12
+    dose = s.run()
+    assert np.array_equal(s.rank_log(), ref["ranks"])
+    err = rel_l2(dose, ref["dose"])
+    print(f"solver with the energy-DG source (straggling {straggling}): dose error {err:.2e}")
+    assert err < 1e-9
+    s.close()
