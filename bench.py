@@ -81,8 +81,9 @@ def _workload(name=WORKLOAD):
     return getattr(WL, name)()
 
 
-# streaming-stage kernels by variant: name and the markers of their source text in device.cuh
-# (the DRAM traffic of a capture is reported only while that text is unchanged)
+# streaming-stage kernels by variant: name and the markers of their source text (device.cuh
+# unless a file is given; the DRAM traffic of a capture is reported only while that text is
+# unchanged)
 STAGE_KERNELS = {
     0: ("kstage_kernel", "template <typename T, int RM, int NACT>\n__global__ void __launch_bounds__(128) kstage_kernel(",
         "// The streaming stage of kstage_kernel on the FP32 path with two"),
@@ -93,7 +94,8 @@ STAGE_KERNELS = {
     4: ("kstage_tma_kernel", None, None),
     5: ("kstage_tma_kernel", None, None),
     6: ("kstage_tmap_kernel", None, None),
-    7: ("kstage_tmaa_kernel", None, None),
+    7: ("kstage_tmaa_kernel", "template <int RM>\n__global__ void __launch_bounds__(192) kstage_tmaa_kernel(",
+        "}  // namespace dlra", "kstage_tma.cuh"),
 }
 STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
                "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7}
@@ -102,10 +104,12 @@ STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs
 def stage_source_sha256(variant):
     """sha256 of the source text of a streaming-stage kernel, or None without markers."""
     import hashlib
-    _, begin, end = STAGE_KERNELS[variant]
+    rec = STAGE_KERNELS[variant]
+    begin, end = rec[1], rec[2]
+    fname = rec[3] if len(rec) > 3 else "device.cuh"
     if begin is None or end is None:
         return None
-    src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", "device.cuh")).read()
+    src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", fname)).read()
     i = src.find(begin)
     j = src.find(end, i + 1) if i >= 0 else -1
     if i < 0 or j < i:
@@ -113,9 +117,11 @@ def stage_source_sha256(variant):
     return hashlib.sha256(src[i:j].encode()).hexdigest()
 
 
-def _stage_traffic(variant, workload=WORKLOAD):
+def _stage_traffic(variant, workload=WORKLOAD, n=None, mean_words=None):
     """DRAM bytes per launch of the streaming-stage kernel in use on this workload from the
-    committed ncu summary, or None when there is none or the kernel's source changed since."""
+    committed ncu summary, or None when there is none or the kernel's source changed since.
+    A capture of a smaller case of the workload records its bytes per cell and (5r + 1) word;
+    they are scaled to n cells and the solve's mean (5r + 1) words per cell and launch."""
     name = STAGE_KERNELS[variant][0]
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
     if not os.path.exists(path):
@@ -127,6 +133,10 @@ def _stage_traffic(variant, workload=WORKLOAD):
     h = stage_source_sha256(variant)
     if h is None or d.get("source_sha256") != h:
         return None, "kernel changed since the capture"
+    if "dram_bytes_per_cell_word" in d and n is not None and mean_words is not None:
+        return float(d["dram_bytes_per_cell_word"]) * n * mean_words, (
+            d.get("capture", "") + f" (captured on {d['cells']} cells at rank {d['rank']}; scaled to {n} cells and "
+            f"{mean_words:.1f} words per cell)")
     return float(d["dram_bytes_per_launch"]), d.get("capture", "")
 
 
@@ -571,7 +581,8 @@ def main():
         STAGE_NAMES.get(tuned["stage_variant"], 0) if tuned else 0)
     if variant == 3 and cfg["nx"] % 2:
         variant = 0
-    traffic, traffic_note = _stage_traffic(variant, name)
+    esize = 8 if cfg["precision"] == 0 else 4
+    traffic, traffic_note = _stage_traffic(variant, name, n, avg_bytes / (n * esize))
     traffic_gbs = traffic / (avg_launch_ms / 1000.0) / 1e9 if traffic else None
     kname = f"{STAGE_KERNELS[variant][0]} (fused RK4 streaming stage: stencil + r x r mix)"
     common = {"traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_launch": avg_bytes,

@@ -24,24 +24,28 @@ def bench():
 
 
 def test_stage_kernel_markers_delimit_each_kernel(bench):
-    src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", "device.cuh")).read()
-    for v, (name, begin, end) in bench.STAGE_KERNELS.items():
+    for v, rec in bench.STAGE_KERNELS.items():
+        name, begin, end = rec[:3]
         if begin is None or end is None:
             continue
+        fname = rec[3] if len(rec) > 3 else "device.cuh"
+        src = open(os.path.join(ROOT, "paper_2508_04484_gb300", "csrc", fname)).read()
         i = src.find(begin)
         j = src.find(end, i + 1)
         assert 0 <= i < j, name
         # the delimited text is that kernel's definition and no other stage kernel's
         text = src[i:j]
         assert f"{name}(" in text
-        others = [n for w, (n, _, _) in bench.STAGE_KERNELS.items() if w != v]
+        others = [r[0] for w, r in bench.STAGE_KERNELS.items() if w != v and r[0] != name]
         assert not any(f" {o}(" in text for o in others), name
         assert bench.stage_source_sha256(v) is not None
 
 
 def test_traffic_record_matches_the_current_sources(bench):
     path = os.path.join(ROOT, "profiles", "kstage_traffic.json")
-    names = {n: v for v, (n, _, _) in bench.STAGE_KERNELS.items()}
+    names = {}
+    for v, rec in bench.STAGE_KERNELS.items():
+        names.setdefault(rec[0], v)
     for workload, wrec in json.load(open(path))["workloads"].items():
         assert workload in bench.WORKLOADS
         for name, rec in wrec["kernels"].items():
