@@ -567,21 +567,24 @@ namespace dlra {
 // (tcgen05.st) and the products read A from there (tcgen05.mma with an A address in TMEM), so
 // neither the operand stores nor the tensor core's A reads use shared memory, which the halo
 // reads and the B reads keep to themselves. TMEM: the accumulator in columns [0, NP), the A
-// stages at 64 + 48 s (hi at +0, lo at +24); 256 columns, two blocks per SM.
+// stages at 64 + 48 s (hi at +0, lo at +24), a three-stage ring; 256 columns, two blocks per SM.
+// The formation threads load their cell's state row for the epilogue while the last products run.
 template <int RM>
 struct KsTmaA {
   using Base = KsTma<RM, 1>;
   static constexpr int NK = 6, CC = 4, KC = 24, NP = Base::NP;
   static constexpr int TX = 8, TY = 4, TZ = 4, BX = 16, BY = 8, BZ = 8, HALO = BX * BY * BZ;
-  static constexpr int TCOLS = 256, ACOL = 64;
+  static constexpr int NS = 3;                                     // ring stages (halo, B, A in TMEM)
+  static constexpr int TCOLS = 256, ACOL = 64;                     // A stage s at ACOL + 48 s
   static constexpr int THREADS = 192;                              // 4 formation, producer, MMA warps
   static constexpr size_t al(size_t b) { return (b + 1023) / 1024 * 1024; }
   static constexpr uint32_t BIMG_BYTES = Base::BIMG_BYTES;
   static constexpr size_t OFF_B = 0;
   static constexpr size_t OFF_H = al(BIMG_BYTES);
   static constexpr size_t STAGE = OFF_H + al((size_t)CC * HALO * 4);
-  static constexpr size_t SMEM = 2 * STAGE + 1024;
+  static constexpr size_t SMEM = NS * STAGE + 1024;
   static constexpr uint32_t HALO_BYTES = CC * HALO * 4;
+  static_assert(ACOL + 48 * NS <= TCOLS, "A stages exceed the TMEM allocation");
 };
 
 template <int RM>
@@ -590,11 +593,11 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
     float* __restrict__ vout, long long ld, const float* __restrict__ inv_rho, Geo g,
     const float* __restrict__ Bimg, const int* __restrict__ rdim, float beta, int mode, int* err) {
   using C = KsTmaA<RM>;
-  constexpr int NK = C::NK, CC = C::CC, KC = C::KC, NP = C::NP, TCOLS = C::TCOLS, ACOL = C::ACOL;
+  constexpr int NK = C::NK, CC = C::CC, KC = C::KC, NP = C::NP, TCOLS = C::TCOLS, ACOL = C::ACOL, NS = C::NS;
   constexpr int TX = C::TX, TY = C::TY, BX = C::BX, BY = C::BY, HALO = C::HALO;
   extern __shared__ unsigned char raw_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)raw_dyn + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[2], afull_bar[2], free_bar[2], acc_bar;
+  __shared__ __align__(8) uint64_t full_bar[NS], afull_bar[NS], free_bar[NS], acc_bar;
   __shared__ uint32_t tslot;
   __shared__ volatile int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -602,7 +605,7 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
   const int nch = (r + CC - 1) / CC;
   if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&full_bar[s], 1);
       tc::mbar_init(&afull_bar[s], 4);
       tc::mbar_init(&free_bar[s], 1);
@@ -625,9 +628,9 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
     int issued = 0;
     if (lane == 0) {
       for (int ch = 0; ch < nch; ++ch) {
-        const int s = ch & 1;
-        if (ch >= 2 &&
-            (s_bad || !tc::mbar_wait_ns(&free_bar[s], (uint32_t)(((ch - 2) >> 1) & 1), tc::kWaitNs))) {
+        const int s = ch % NS;
+        if (ch >= NS &&
+            (s_bad || !tc::mbar_wait_ns(&free_bar[s], (uint32_t)(((ch - NS) / NS) & 1), tc::kWaitNs))) {
           s_bad = 1;
           break;
         }
@@ -636,8 +639,8 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
         tc::bulk_load(stage_ptr(s, C::OFF_B), Bimg + (size_t)ch * (C::BIMG_BYTES / 4), C::BIMG_BYTES, &full_bar[s]);
         issued = ch + 1;
       }
-      for (int ch = (issued >= 2 ? issued - 2 : 0); ch < issued; ++ch)
-        tc::mbar_wait_ns(&full_bar[ch & 1], (uint32_t)((ch >> 1) & 1), tc::kWaitNs);
+      for (int ch = (issued >= NS ? issued - NS : 0); ch < issued; ++ch)
+        tc::mbar_wait_ns(&full_bar[ch % NS], (uint32_t)((ch / NS) & 1), tc::kWaitNs);
     }
   } else if (warp == 5) {
     // ---------------- products: A from TMEM, B from shared memory ----------------
@@ -645,8 +648,8 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
       constexpr uint32_t idesc = tc::idesc_tf32(128, NP);
       constexpr uint32_t bLBO = (NP / 8) * 128;
       for (int ch = 0; ch < nch; ++ch) {
-        const int s = ch & 1;
-        if (s_bad || !tc::mbar_wait_ns(&afull_bar[s], (uint32_t)((ch >> 1) & 1), tc::kWaitNs)) {
+        const int s = ch % NS;
+        if (s_bad || !tc::mbar_wait_ns(&afull_bar[s], (uint32_t)((ch / NS) & 1), tc::kWaitNs)) {
           s_bad = 1;
           break;
         }
@@ -679,9 +682,9 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
     const int hc = (lz + 2) * SZ + (ly + 2) * SY + (lx + 4);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     for (int ch = 0; ch < nch; ++ch) {
-      const int s = ch & 1;
+      const int s = ch % NS;
       // the warp decides together: tcgen05.st is warp-collective
-      bool go = !s_bad && tc::mbar_wait_ns(&full_bar[s], (uint32_t)((ch >> 1) & 1), tc::kWaitNs);
+      bool go = !s_bad && tc::mbar_wait_ns(&full_bar[s], (uint32_t)((ch / NS) & 1), tc::kWaitNs);
       go = __all_sync(0xffffffffu, go);
       if (!go) {
         s_bad = 1;
@@ -714,6 +717,16 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
       if (lane == 0) tc::mbar_arrive(&afull_bar[s]);
     }
   }
+  // the epilogue's state values, loaded while the last products run
+  float yv[NP];
+  if (warp < 4) {
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+    const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+    const long long i = ((long long)iz * g.ny + iy) * g.nx + ix;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) yv[c] = (ok && c < RM) ? y[(long long)c * ld + i] : 0.f;
+  }
   __syncthreads();
   const bool alive = s_bad == 0;
   if (warp < 4) {
@@ -734,9 +747,6 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
           for (int j = 0; j < 16; ++j) acc[j] = 0.f;
         }
         if (!ok) continue;
-        float yv[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) yv[j] = (c0 + j < RM) ? y[(long long)(c0 + j) * ld + i] : 0.f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = c0 + j;
@@ -745,13 +755,13 @@ __global__ void __launch_bounds__(192) kstage_tmaa_kernel(
           if (mode == 2) {
             const float lam = beta * ir0 * acc[j];
             vout[e] = lam;
-            yout[e] = yv[j] + lam;
+            yout[e] = yv[c] + lam;
           } else if (mode == 1) {
-            const float yn = yv[j] + beta * acc[j];
+            const float yn = yv[c] + beta * acc[j];
             yout[e] = yn;
             vout[e] = ir0 * yn;
           } else {
-            vout[e] = ir0 * (yv[j] + beta * acc[j]);
+            vout[e] = ir0 * (yv[c] + beta * acc[j]);
           }
         }
       }
