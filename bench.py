@@ -96,9 +96,12 @@ STAGE_KERNELS = {
     6: ("kstage_tmap_kernel", None, None),
     7: ("kstage_tmaa_kernel", "template <int RM>\n__global__ void __launch_bounds__(192) kstage_tmaa_kernel(",
         "}  // namespace dlra", "kstage_tma.cuh"),
+    8: ("kstage_tmac_kernel", "template <int RM>\n__global__ void __launch_bounds__(192) kstage_tmac_kernel(",
+        "}  // namespace dlra", "kstage_tmac.cuh"),
 }
 STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
-               "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7}
+               "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7,
+               "TMA tensor cores cluster": 8}
 
 
 def stage_source_sha256(variant):

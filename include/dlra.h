@@ -229,13 +229,15 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * streaming stage per cell with FMA, on the tensor cores (FP32 path) or per brick with FMA and
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
- * kernel). Needs materials and a beam; synchronises; drops captured graphs. report (optional,
- * 20 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 .. 5 as dlra_set_stage_kernel), Gram block
+ * kernel) and of the truncation apply (FMA or tensor cores). Needs materials and a beam;
+ * synchronises; drops captured graphs. report (optional, 24 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 .. 8 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
  * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
- * of its form with A in tensor memory (-1 where not applicable). */
+ * of its form with A in tensor memory, ms of the truncation apply with FMA and on the tensor
+ * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage
+ * (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -249,9 +251,19 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * that streams its bricks' chunks through a four-deep TMA ring and drains one brick's TMEM
  * accumulator while the next brick accumulates in a second one, 7 the 128-cell form with the
  * A operand (the stencil values) written to tensor memory (tcgen05.st) and read from there by
- * the products, leaving shared memory to the halo and B. Same results up to rounding;
- * dlra_autotune picks among them. */
+ * the products, leaving shared memory to the halo and B, 8 variant 7 on clusters of two CTAs
+ * owning y-adjacent bricks: one multicast TMA copy loads the pair's common halo box and one
+ * multicast bulk copy the chunk's B image into both CTAs (variant 7 where the cluster launch is
+ * refused). Same results up to rounding; dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
+
+/* Kernel of the cell-side tall-skinny products (the augmentation's projections and the
+ * truncation's X = X^ P, Sec. 2.2): 0 one thread per cell with FMA (default), 1 on the tensor
+ * cores (FP32 path, at least 65,536 cells and 16 output columns: each 128-cell tile of A loaded
+ * by TMA, split into TF32 high and low parts into tensor memory, tcgen05.mma kind::tf32 with
+ * FP32 accumulation; the FMA kernel otherwise), 2 as 1 at any cell count. Same results up to
+ * rounding; dlra_autotune picks between 0 and 1. */
+dlra_status dlra_set_apply_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):
  * 0 FMA (default), 1 on the tensor cores (FP32-mixed path only: tcgen05.mma kind::tf32 with

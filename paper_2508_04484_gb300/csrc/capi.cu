@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -36,6 +37,8 @@
 #include "kernels.h"
 #include "kstage_tc.cuh"
 #include "kstage_tma.cuh"
+#include "kstage_tmac.cuh"
+#include "apply_tc.cuh"
 #include "tables.h"
 
 using namespace dlra;
@@ -213,9 +216,12 @@ struct Tuning {
   int gs_waves_x2 = 2;        // stencil Gram grid: (gs_waves_x2 / 2) x (blocks per SM) x SMs blocks
   int kstage_variant = 0;     // streaming stage: 0 per-cell FMA, 1 tcgen05 (FP32 path), 2 brick-staged FMA,
                               // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks,
-                              // 6 its persistent form, 7 with the A operand in tensor memory
+                              // 6 its persistent form, 7 with the A operand in tensor memory, 8 that on
+                              // 2-CTA clusters with multicast halo and B copies
   int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
+  int apply_variant = 0;      // tall-skinny applies: 0 FMA, 1 tcgen05 (FP32 path, tall, 16 <= N, Q <= 128),
+                              // 2 tcgen05 at any height
 };
 thread_local const Tuning* t_tuning = nullptr;
 const Tuning& tuning() {
@@ -392,11 +398,54 @@ bool kstage_tmaa_launch(cudaStream_t st, const float* vin, const float* y, float
   return true;
 }
 
+// cluster launches of the stage that the runtime refused (their work ran as variant 7)
+std::atomic<long long> g_tmac_refused{0};
+
+// the A-in-TMEM stage on clusters of two y-adjacent bricks sharing one multicast halo box and
+// B image; false when the layout rules are not met or the cluster launch is refused
+template <int RM>
+bool kstage_tmac_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                        int* err, void* bimg) {
+  using C = KsTmaC<RM>;
+  using B1 = KsTma<RM, 1>;
+  if (!bimg) return false;
+  CUtensorMap m;
+  if (!stage_tensor_map(&m, vin, g, n, RM, C::BY)) return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  kstage_tma_bimg_kernel<RM, 1><<<nblk((long long)B1::NCH * B1::NP * B1::KC, 256), 256, 0, st>>>(Pst, rdim, img);
+  cudaFuncSetAttribute(kstage_tmac_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kstage_tmac_grid<RM>(g), 1, 1);
+  cfg.blockDim = dim3(C::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const Geo gg = g;
+  if (cudaLaunchKernelEx(&cfg, kstage_tmac_kernel<RM>, m, y, yout, vout, n, inv_rho, gg, (const float*)img, rdim, beta,
+                         last, err) != cudaSuccess) {
+    cudaGetLastError();
+    g_tmac_refused.fetch_add(1);
+    return false;
+  }
+  return true;
+}
+
 template <typename T, int RM, int NACT>
 void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, long long n, const T* inv_rho,
                    const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant,
                    void* bimg) {
   if constexpr (sizeof(T) == 4 && NACT == 3 && RM >= 32) {
+    if (variant == 8) {
+      if (kstage_tmac_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
+      variant = 7;
+    }
     if (variant == 7) {
       if (kstage_tmaa_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
       variant = 0;
@@ -524,12 +573,63 @@ void apply_launch(cudaStream_t st, long long rows, const T* A, long long lda, in
                                                           V, inv_rho);
 }
 
-// C(:, :N) = alpha A(:, :Q) M + beta Cin (+ V = rho^-1 C); N <= 64
+// Work space of the tensor-core apply: the B image of one launch (64 KB) and the error word.
+struct ApplyTc {
+  void* img = nullptr;
+  int* err = nullptr;
+};
+
+// the tensor-core apply at MMA width NP (FP32, Q <= 128, N <= NP); false when A does not meet
+// the tensor map's rules (the caller falls back to the FMA kernel)
+template <int NP>
+bool apply_tc_launch(cudaStream_t st, long long rows, const float* A, long long lda, int Q, const int* qdim,
+                     const double* M, long long ldm, int N, float* C, long long ldc, const float* Cin, float alpha,
+                     float beta, float* V, const float* inv_rho, const ApplyTc& tcw) {
+  using Cf = ApTc<NP>;
+  if (lda % 4 != 0 || ((uintptr_t)A & 15u) != 0 || Q > Cf::QMAX || N > NP) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)Q};
+  const cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
+  const cuuint32_t box[2] = {128, (cuuint32_t)Cf::KCH};
+  const cuuint32_t es[2] = {1, 1};
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  float* img = reinterpret_cast<float*>(tcw.img);
+  apply_tc_bimg_kernel<NP><<<nblk((long long)NP * Cf::QMAX, 256), 256, 0, st>>>(M, ldm, Q, qdim, N, img);
+  cudaFuncSetAttribute(apply_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
+  apply_tc_kernel<NP><<<(unsigned)((rows + 127) / 128), Cf::THREADS, Cf::SMEM, st>>>(
+      m, rows, Q, qdim, img, N, C, ldc, Cin, alpha, beta, V, inv_rho, tcw.err);
+  return true;
+}
+
+// C(:, :N) = alpha A(:, :Q) M + beta Cin (+ V = rho^-1 C); N <= 64. With tcw (FP32, 16 <= N,
+// Q <= 128, tuning().apply_variant 1 with at least 65,536 rows or 2) on the tensor cores, else
+// the FMA kernel.
 template <typename T>
 void apply(cudaStream_t st, long long rows, const T* A, long long lda, int Q, const int* qdim, const double* M,
            long long ldm, int N, T* C, long long ldc, const T* Cin, T alpha, T beta, int64_t& nl, T* V = nullptr,
-           const T* inv_rho = nullptr) {
+           const T* inv_rho = nullptr, const ApplyTc* tcw = nullptr) {
   if (rows <= 0 || N <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    const int av = tuning().apply_variant;
+    if (tcw && tcw->img && ((av == 1 && rows >= 65536) || av == 2) && N >= 16 && Q <= 128) {
+      bool done = false;
+      if (N <= 32)
+        done = apply_tc_launch<32>(st, rows, A, lda, Q, qdim, M, ldm, N, C, ldc, Cin, alpha, beta, V, inv_rho, *tcw);
+      else if (N <= 48)
+        done = apply_tc_launch<48>(st, rows, A, lda, Q, qdim, M, ldm, N, C, ldc, Cin, alpha, beta, V, inv_rho, *tcw);
+      else
+        done = apply_tc_launch<64>(st, rows, A, lda, Q, qdim, M, ldm, N, C, ldc, Cin, alpha, beta, V, inv_rho, *tcw);
+      if (done) {
+        nl += 2;
+        return;
+      }
+    }
+  }
   const int nm = N <= 4 ? 4 : N <= 8 ? 8 : N <= 12 ? 12 : N <= 16 ? 16 : N <= 20 ? 20 : N <= 24 ? 24
                : N <= 32 ? 32 : N <= 40 ? 40 : N <= 48 ? 48 : 64;
   switch (nm) {
@@ -626,6 +726,7 @@ struct Lane {
   void* Kw = nullptr;        // the source's moment factor in the n-side type (FP32 paths)
   void* svdV = nullptr;      // right rotations of the truncation SVD when they do not fit shared memory
   void* Bimg = nullptr;      // B-operand images of the TMA-staged tensor-core stage
+  ApplyTc atc;               // tensor-core applies of the cell side (B image, error word)
   SstepWork sgw;             // grid-parallel S-step (2r beyond the cluster kernel's shared memory)
 };
 
@@ -910,7 +1011,8 @@ struct Engine {
     cudaMemsetAsync(L->C1, 0, sizeof(double) * RB * qcap, st);
     gram<T>(st, n, B.X, n, rdim, RB, qcap, FPlain<T>{K, n, nullptr, qcap}, L->C1, RB, nl);
     // R = K - X C1 into X^[:, RB:RB+qcap]
-    apply<T>(st, n, B.X, n, RB, rdim, L->C1, RB, qcap, Xh + (long long)RB * n, n, K, T(-1), T(1), nl);
+    apply<T>(st, n, B.X, n, RB, rdim, L->C1, RB, qcap, Xh + (long long)RB * n, n, K, T(-1), T(1), nl, nullptr, nullptr,
+             &L->atc);
     for (int pass = 0; pass < 2; ++pass) {
       const int lg = RB + qcap;
       cudaMemsetAsync(L->Cg, 0, sizeof(double) * lg * qcap, st);
@@ -918,7 +1020,8 @@ struct Engine {
       launch_orth_factor(st, L->Cg, pass == 0 ? L->C1 : nullptr, RB, qcap, pass == 0 ? drop1() : drop2(),
                          L->Mapply, &B.dims->qx, ctx->dev_err);
       ++nl;
-      apply<T>(st, n, Xh, n, lg, nullptr, L->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl);
+      apply<T>(st, n, Xh, n, lg, nullptr, L->Mapply, lg, qcap, Xh + (long long)RB * n, n, nullptr, T(1), T(0), nl,
+               nullptr, nullptr, &L->atc);
     }
   }
 
@@ -952,7 +1055,8 @@ struct Engine {
     const long long n = ctx->n;
     const int RB = ctx->RB, n2 = ctx->n2, m = ctx->m;
     int64_t& nl = ctx->launches;
-    apply<T>(L->s0, n, P(L->Xh), n, n2, nullptr, L->Pt, n2, RB, B.X, n, nullptr, T(1), T(0), nl);
+    apply<T>(L->s0, n, P(L->Xh), n, n2, nullptr, L->Pt, n2, RB, B.X, n, nullptr, T(1), T(0), nl, nullptr, nullptr,
+             &L->atc);
     gemm<T, 16>(L->s0, m, RB, n2, ALoadPlain<T>{P(L->Wh), m, nullptr, n2},
                 BLoadCol<T, double>{L->Qt, n2, nullptr, n2, nullptr, RB}, EpiStore<T>{B.W, m, nullptr, m, T(1), T(0)},
                 nl);
@@ -1009,8 +1113,8 @@ struct Engine {
     T* y = P(L->Kb[0]);
     T* va = (cap && !adj) ? capq(0) : P(L->Kb[1]);
     T* vb = P(L->Kb[2]);
-    if (adj) apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl);
-    else apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho));
+    if (adj) apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, nullptr, nullptr, &L->atc);
+    else apply<T>(st, n, B.X, n, RB, rdim, B.S, RB, RB, y, n, nullptr, T(1), T(0), nl, va, P(ctx->inv_rho), &L->atc);
     cudaStreamWaitEvent(st, L->ev[1], 0);   // stage kernel needs P
     cudaStreamWaitEvent(sm, L->ev[2], 0);   // L-stage needs G
     // RK4 Horner stages: K-step on st, L-step on sm
@@ -1361,6 +1465,10 @@ dlra_status alloc_lane(dlra_ctx* ctx) {
   }
   if (sizeof(T) == 4 && ctx->geo.nact == 3 && kstage_tma_bimg_bytes(RB) > 0)
     ALLOC(L.Bimg, kstage_tma_bimg_bytes(RB));
+  if (sizeof(T) == 4) {
+    ALLOC(L.atc.img, ApTc<64>::BBYTES);
+    L.atc.err = ctx->dev_err;
+  }
   const size_t tsmall = ctx->small64 ? sizeof(double) : sizeof(T);   // arithmetic of the SVD and S-step
   if (svd_needs_vwork(n2, tsmall)) ALLOC(L.svdV, tsmall * (size_t)n2 * n2);
   if (sstep_needs_grid(nk, n2, tsmall)) {
@@ -2129,12 +2237,12 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[20] = {0};
+  double rep[24] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
   // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
   // nx % 4 == 0, rank capacity >= 32)
-  double stage_ms[8];
-  for (int v = 0; v < 8; ++v) {
+  double stage_ms[9];
+  for (int v = 0; v < 9; ++v) {
     if ((v == 1 || v == 3 || v >= 4) && sizeof(T) != 4) {
       stage_ms[v] = -1.0;
       continue;
@@ -2147,13 +2255,26 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
       stage_ms[v] = -1.0;
       continue;
     }
+    const long long refused = g_tmac_refused.load();
     stage_ms[v] = time_cold_ms([&] {
       kstage<T>(RB, st, E.P(L.Kb[1]), E.P(L.Kb[0]), E.P(L.Kb[0]), E.P(L.Kb[2]), n, E.P(ctx->inv_rho), ctx->geo,
                 E.P(L.Pst), rdim, T(1e-3), 0, nl, ctx->dev_err, v, L.Bimg);
     });
+    if (v == 8 && g_tmac_refused.load() != refused) stage_ms[v] = -1.0;   // ran as variant 7
   }
   rep[0] = stage_ms[0];
   rep[1] = stage_ms[1];
+  // the truncation apply X = X^ P (n x 2RB by 2RB x RB): FMA against tensor cores (FP32 path)
+  double apply_ms[2] = {-1.0, -1.0};
+  for (int v = 0; v < 2; ++v) {
+    if (v == 1 && (sizeof(T) != 4 || n < 65536 || RB < 16)) continue;
+    t.apply_variant = v;
+    apply_ms[v] = time_cold_ms([&] {
+      apply<T>(st, n, E.P(L.Xh), n, n2, nullptr, L.Pt, n2, RB, E.P(L.Kb[2]), n, nullptr, T(1), T(0), nl, nullptr,
+               nullptr, &L.atc);
+    });
+  }
+  t.apply_variant = 0;
   // Gram reduction X^_{:, RB:}^T X^ (the second augmentation pass's shape)
   const int gb[4] = {608, 1216, 2432, 4864};
   for (int v = 0; v < 4; ++v) {
@@ -2189,7 +2310,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   cudaFree(flush);
   Tuning best = ctx->tun;
   int sv = 0;
-  for (int v = 1; v < 8; ++v)
+  for (int v = 1; v < 9; ++v)
     if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
   best.kstage_variant = sv;
   int bi = 0;
@@ -2210,6 +2331,11 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   rep[17] = stage_ms[5];
   rep[18] = stage_ms[6];
   rep[19] = stage_ms[7];
+  rep[23] = stage_ms[8];
+  best.apply_variant = (apply_ms[1] > 0.0 && apply_ms[1] < apply_ms[0]) ? 1 : 0;
+  rep[20] = apply_ms[0];
+  rep[21] = apply_ms[1];
+  rep[22] = best.apply_variant;
   rep[10] = best.gram_blocks;
   rep[11] = best.gs_waves_x2;
   ctx->tun = best;
@@ -2649,10 +2775,20 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 7) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 7");
+  if (variant < 0 || variant > 8) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 8");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;
+  return DLRA_OK;
+}
+
+dlra_status dlra_set_apply_kernel(dlra_ctx* ctx, int32_t variant) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (variant < 0 || variant > 2) return fail(ctx, DLRA_ERR_ARG, "apply kernel variant must be 0, 1 or 2");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->tun.apply_variant = variant;
   return DLRA_OK;
 }
 

@@ -136,6 +136,58 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0,
       : "memory");
 }
 
+// TMA: a 2-D box (c0 innermost) of the tensor described by the tensor map into shared memory
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(su32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(su32(bar))
+      : "memory");
+}
+
+// TMA 4-D box multicast to the CTAs of the cluster in cta_mask (same shared-memory offset and
+// barrier offset in each)
+__device__ __forceinline__ void tma_load_4d_mc(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                               uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
+      "[%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(su32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// bulk copy multicast to the CTAs of the cluster in cta_mask
+__device__ __forceinline__ void bulk_load_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// arrive on the barrier at this offset in every CTA of cta_mask once the tcgen05 operations
+// issued so far by this thread are done
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          su32(bar)),
+      "h"(cta_mask)
+      : "memory");
+}
+
+// rank of this CTA in its cluster
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// barrier over all threads of all CTAs of the cluster (release / acquire at cluster scope)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // bulk copy of `bytes` contiguous bytes from global to shared memory (both 16-byte aligned,
 // bytes a multiple of 16); completion counted on the barrier
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -128,26 +128,14 @@ def test_workload_kernel_instances_match_oracle(kind, precision):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8])
 @pytest.mark.parametrize("case", ["ragged", "phantom_128cube"])
 def test_tma_tensor_core_stage_matches_oracle(case, variant):
     # the TMA-staged tensor-core streaming stage (128- and 256-cell bricks) against the per-cell
     # FMA stage and the oracle: on a grid whose bricks are ragged in every direction (rank
     # capacity 40, MMA N = 48) and at the 128^3 phantom workload's widths (capacity 64)
     if case == "ragged":
-        cfg = WL.base_config(nx=20, ny=18, nz=10, dx=0.2, dy=0.2, dz=0.2, N=7, collision=WL.BOLTZMANN,
-                             rank_mode=WL.FIXED, rank=40, rank_max=40, e_max=120.0, e_min=118.0, n_steps=2,
-                             precision=WL.FP32_MIXED)
-        mats, w = WL.ellipsoid_phantom(cfg, 9, n_incl=3, semi=(0.3, 0.9))
-        beams = [WL.pencil_beam(120.0, (1.71, 1.53, 0.0), (0.1, 0.07, 1.0), spot_sigma=0.1)]
-        prob = oracle_problem(cfg, mats, w)
-        src = oracle_sources(prob, beams)
-        X, S, W = _state(prob, 40, 23)
-        st = ODL.State(prob.n, prob.m)
-        st.X, st.S, st.W = X.copy(), S.copy(), W.copy()
-        log = []
-        for k in range(prob.K):
-            ODL.step(prob, st, k, src, ODL.RankControl(mode=OP.FIXED, rank=40), log=log)
+        cfg, mats, w, beams, prob, (X, S, W), st, log = _ragged_instance()
     else:
         cfg, mats, w, beams, r, mode, kw = _instance(case, WL.FP32_MIXED)
         prob, src, (X, S, W), st, log, _ = _oracle_run(case)
@@ -163,4 +151,49 @@ def test_tma_tensor_core_stage_matches_oracle(case, variant):
     e_fma, e_or = rel_l2(us[1], us[0]), rel_l2(us[1], st.u())
     print(f"TMA stage variant {variant} on {case}: against the FMA stage {e_fma:.2e}, against the oracle {e_or:.2e}")
     assert e_fma < 1e-5
+    assert e_or < 1e-3
+
+
+def _ragged_instance():
+    # a grid whose 128-cell tiles and bricks are ragged in every direction (3,600 cells), rank 40
+    # (MMA N = 48), advanced by the oracle over two energy steps from a seeded state
+    cfg = WL.base_config(nx=20, ny=18, nz=10, dx=0.2, dy=0.2, dz=0.2, N=7, collision=WL.BOLTZMANN,
+                         rank_mode=WL.FIXED, rank=40, rank_max=40, e_max=120.0, e_min=118.0, n_steps=2,
+                         precision=WL.FP32_MIXED)
+    mats, w = WL.ellipsoid_phantom(cfg, 9, n_incl=3, semi=(0.3, 0.9))
+    beams = [WL.pencil_beam(120.0, (1.71, 1.53, 0.0), (0.1, 0.07, 1.0), spot_sigma=0.1)]
+    prob = oracle_problem(cfg, mats, w)
+    src = oracle_sources(prob, beams)
+    X, S, W = _state(prob, 40, 23)
+    st = ODL.State(prob.n, prob.m)
+    st.X, st.S, st.W = X.copy(), S.copy(), W.copy()
+    log = []
+    for k in range(prob.K):
+        ODL.step(prob, st, k, src, ODL.RankControl(mode=OP.FIXED, rank=40), log=log)
+    return cfg, mats, w, beams, prob, (X, S, W), st, log
+
+
+@pytest.mark.parametrize("case", ["ragged", "phantom_128cube"])
+def test_tensor_core_apply_matches_oracle(case):
+    # the cell-side tall-skinny products on the tensor cores (augmentation projections, the
+    # truncation's X = X^ P), forced at every height (kernel 2), on ragged 128-row tiles and at
+    # the 128^3 phantom workload's widths: against the FMA products and the oracle
+    if case == "ragged":
+        cfg, mats, w, beams, prob, (X, S, W), st, log = _ragged_instance()
+    else:
+        cfg, mats, w, beams, r, mode, kw = _instance(case, WL.FP32_MIXED)
+        prob, src, (X, S, W), st, log, _ = _oracle_run(case)
+    us = []
+    for v in (0, 2):
+        s = gpu_solver(cfg, mats, w, beams, schedule=np.asarray(log, dtype=np.int32), precision=WL.FP32_MIXED)
+        s.set_apply_kernel(v)
+        s.set_state(X, S, W)
+        s.step(prob.K)
+        Xg, Sg, Wg = s.get_state()
+        us.append(Xg @ Sg @ Wg.T)
+        s.close()
+    e_fma, e_or = rel_l2(us[1], us[0]), rel_l2(us[1], st.u())
+    print(f"tensor-core apply on {case}: against the FMA products {e_fma:.2e}, against the oracle {e_or:.2e}")
+    # the two kernels round differently: equal results would mean the tensor-core path never ran
+    assert 0.0 < e_fma < 1e-5
     assert e_or < 1e-3
