@@ -218,7 +218,7 @@ struct Tuning {
                               // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks,
                               // 6 its persistent form, 7 with the A operand in tensor memory, 8 that on
                               // 2-CTA clusters with multicast halo and B copies
-  int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path)
+  int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path), 2 tcgen05 with a TMA window (A == B, 3-D)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
   int apply_variant = 0;      // tall-skinny applies: 0 FMA, 1 tcgen05 (FP32 path, tall, 16 <= N, Q <= 128),
                               // 2 tcgen05 at any height
@@ -301,19 +301,7 @@ constexpr int kRankCaps[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
 
 // cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query: the library
 // links only the runtime)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }();
-  return fn;
-}
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return tma_encode_fn(); }
 
 // The streaming-stage input (rcap columns of ld floats, each an nx x ny x nz grid, x fastest)
 // as a 4-D tensor for TMA, box 16 x box_y x 8 x 4 (x, y, z, column). Needs nx and ld multiples
@@ -532,7 +520,12 @@ void gram_stencil(cudaStream_t st, long long rows, const T* A, long long lda, in
                   long long ldb, int nb, const int* bdim, const T* inv_rho, const Geo& g, double* out, int ldj,
                   long long ldo, int64_t& nl, int* err = nullptr) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tuning().gs_variant == 1 && gram_stencil_tc_supported(na, rows)) {
+    if (tuning().gs_variant == 2 &&
+        launch_gram_stencil_win(st, rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, out, ldj, ldo, err)) {
+      ++nl;
+      return;
+    }
+    if (tuning().gs_variant >= 1 && gram_stencil_tc_supported(na, rows)) {
       launch_gram_stencil_tc(st, rows, A, lda, na, adim, B, ldb, nb, bdim, inv_rho, g, out, ldj, ldo,
                              tuning().gs_tc_waves_x2, err);
       ++nl;
@@ -2237,7 +2230,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[24] = {0};
+  double rep[25] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
   // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
   // nx % 4 == 0, rank capacity >= 32)
@@ -2294,13 +2287,20 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
     });
   }
   // the same stencil Gram on the tensor cores (FP32 path)
-  double gs_tc_ms = -1.0;
+  double gs_tc_ms = -1.0, gs_win_ms = -1.0;
+  const bool gram_win_applies = ctx->geo.nact == 3 && ctx->geo.nx % 4 == 0 && n % 4 == 0 && n2 <= 128;
   if (sizeof(T) == 4 && gram_stencil_tc_supported(n2, n)) {
     t.gs_variant = 1;
     gs_tc_ms = time_ms([&] {
       gram_stencil<T>(st, n, E.P(L.Xh), n, n2, nullptr, E.P(L.Xh), n, n2, nullptr, E.P(ctx->inv_rho), ctx->geo, L.Gc,
                       n2, n2, nl, ctx->dev_err);
     });
+    t.gs_variant = 2;
+    gs_win_ms = time_ms([&] {
+      gram_stencil<T>(st, n, E.P(L.Xh), n, n2, nullptr, E.P(L.Xh), n, n2, nullptr, E.P(ctx->inv_rho), ctx->geo, L.Gc,
+                      n2, n2, nl, ctx->dev_err);
+    });
+    if (!gram_win_applies) gs_win_ms = -1.0;
     t.gs_variant = 0;
   }
   cudaEventDestroy(e0);
@@ -2322,6 +2322,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
     if (rep[6 + v] < rep[6 + wi]) wi = v;
   best.gs_waves_x2 = gw[wi];
   best.gs_variant = (gs_tc_ms > 0.0 && gs_tc_ms < rep[6 + wi]) ? 1 : 0;
+  if (gs_win_ms > 0.0 && gs_win_ms < (best.gs_variant == 1 ? gs_tc_ms : rep[6 + wi])) best.gs_variant = 2;
+  rep[24] = gs_win_ms;
   rep[13] = gs_tc_ms;
   rep[14] = best.gs_variant;
   rep[9] = best.kstage_variant;
@@ -2804,7 +2806,7 @@ dlra_status dlra_set_tensor_cores(dlra_ctx* ctx, int32_t enable) {
 dlra_status dlra_set_stencil_gram_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 1) return fail(ctx, DLRA_ERR_ARG, "stencil Gram variant must be 0 or 1");
+  if (variant < 0 || variant > 2) return fail(ctx, DLRA_ERR_ARG, "stencil Gram variant must be 0, 1 or 2");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.gs_variant = variant;
@@ -2975,8 +2977,8 @@ dlra_status dlra_stencil_gram(const dlra_stencil_gram_args* a) {
     return DLRA_ERR_ARG;
   }
   if (a->na < 1 || a->na > 128 || a->nb < 1 || a->nb > 128 || a->lda < n || a->ldb < n || a->variant < 0 ||
-      a->variant > 1) {
-    set_context_free_error("need 1 <= na, nb <= 128, lda, ldb >= n and variant 0 or 1");
+      a->variant > 2) {
+    set_context_free_error("need 1 <= na, nb <= 128, lda, ldb >= n and variant 0, 1 or 2");
     return DLRA_ERR_ARG;
   }
   if (!a->A || !a->B || !a->inv_rho || !a->out) {

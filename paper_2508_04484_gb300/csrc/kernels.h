@@ -1,5 +1,7 @@
 // Launch wrappers of the small dense (one thread block) kernels and the ray tracer.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -163,6 +165,16 @@ bool gram_stencil_tc_supported(int na, long long rows);
 void launch_gram_stencil_tc(cudaStream_t st, long long rows, const float* A, long long lda, int na, const int* adim,
                             const float* B, long long ldb, int nb, const int* bdim, const float* inv_rho,
                             const Geo& g, double* out, int ldj, long long ldo, int waves_x2, int* err);
+
+// The same Gram with A == B on a 3-D grid, its inputs staged by TMA in a window that slides
+// along each stencil's axis and the stencil operand written into tensor memory (gram_win.cu).
+// Needs na == nb <= 128, adim == bdim, nx and lda multiples of 4, 16-byte aligned A and
+// inv_rho; returns false (nothing launched) otherwise.
+bool launch_gram_stencil_win(cudaStream_t st, long long rows, const float* A, long long lda, int na,
+                             const int* adim, const float* B, long long ldb, int nb, const int* bdim,
+                             const float* inv_rho, const Geo& g, double* out, int ldj, long long ldo, int* err);
+// cuTensorMapEncodeTiled from the driver (nullptr where it cannot be had)
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn();
 
 // Work-space bytes of one stand-alone K-step (see dlra_kstep) and the step itself on
 // caller-provided device work space of at least that many bytes.

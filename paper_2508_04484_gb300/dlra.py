@@ -357,7 +357,7 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(24)
+    rep = np.zeros(25)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
@@ -370,7 +370,8 @@ def dlra_autotune(ctx):
                                "TMA tensor cores 256", "TMA tensor cores persistent",
                                "TMA tensor cores A in TMEM", "TMA tensor cores cluster")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
-                stencil_gram_kernel=("FMA", "tensor cores")[int(rep[14])])
+                stencil_gram_window_ms=rep[24],
+                stencil_gram_kernel=("FMA", "tensor cores", "tensor cores TMA window")[int(rep[14])])
 
 
 def dlra_set_stage_kernel(ctx, variant: int):
@@ -619,7 +620,7 @@ class Solver:
         dlra_set_stage_kernel(self.ctx, variant)
 
     def set_stencil_gram_kernel(self, variant):
-        """0 FMA, 1 tensor cores (FP32 path)."""
+        """0 FMA, 1 tensor cores (FP32 path), 2 tensor cores with a sliding TMA window (FP32, 3-D; else 1)."""
         dlra_set_stencil_gram_kernel(self.ctx, variant)
 
     def set_tensor_cores(self, enable=True):

@@ -197,3 +197,28 @@ def test_tensor_core_apply_matches_oracle(case):
     # the two kernels round differently: equal results would mean the tensor-core path never ran
     assert 0.0 < e_fma < 1e-5
     assert e_or < 1e-3
+
+
+@pytest.mark.parametrize("case", ["ragged", "phantom_128cube"])
+def test_windowed_stencil_gram_in_solver(case):
+    # the L-step and S-step Galerkin blocks on the tensor cores with the sliding TMA window
+    # (stencil-Gram kernel 2; r x r at capacity 40 / 64 and 2r x 2r at 80 / 128 columns) inside
+    # whole energy steps: against the FMA Grams and the oracle
+    if case == "ragged":
+        cfg, mats, w, beams, prob, (X, S, W), st, log = _ragged_instance()
+    else:
+        cfg, mats, w, beams, r, mode, kw = _instance(case, WL.FP32_MIXED)
+        prob, src, (X, S, W), st, log, _ = _oracle_run(case)
+    us = []
+    for v in (0, 2):
+        s = gpu_solver(cfg, mats, w, beams, schedule=np.asarray(log, dtype=np.int32), precision=WL.FP32_MIXED)
+        s.set_stencil_gram_kernel(v)
+        s.set_state(X, S, W)
+        s.step(prob.K)
+        Xg, Sg, Wg = s.get_state()
+        us.append(Xg @ Sg @ Wg.T)
+        s.close()
+    e_fma, e_or = rel_l2(us[1], us[0]), rel_l2(us[1], st.u())
+    print(f"windowed stencil Gram on {case}: against the FMA Grams {e_fma:.2e}, against the oracle {e_or:.2e}")
+    assert 0.0 < e_fma < 1e-5
+    assert e_or < 1e-3

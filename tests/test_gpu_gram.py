@@ -1,8 +1,8 @@
 """GPU parity of the stencil Gram G_k[a][b] = sum_i A(i, a) D_k(rho^-1 B(:, b))(i), the Galerkin
 blocks of the streaming operator in the L-step and S-step (Sec. 3.3.2), through the stand-alone
-C-ABI entry point dlra_stencil_gram: the FMA kernel and the tensor-core kernel (tcgen05 kind::tf32
-with high/low splits) against the oracle's stencils (oracle/grid.py apply_D) in FP64 on the same
-FP32 inputs."""
+C-ABI entry point dlra_stencil_gram: the FMA kernel, the tensor-core kernel (tcgen05 kind::tf32
+with high/low splits) and the tensor-core kernel with a sliding TMA window (A == B, 3-D) against
+the oracle's stencils (oracle/grid.py apply_D) in FP64 on the same FP32 inputs."""
 import numpy as np
 import pytest
 
@@ -110,3 +110,76 @@ def test_stencil_gram_rejects_bad_arguments():
     r = torch.ones(64, dtype=torch.float32, device=dev)
     with pytest.raises(D.DlraError):
         D.stencil_gram((4, 4, 4), (0.1, 0.1, 0.1), X, X, r)
+
+
+def _kernel_names(fn):
+    # names of the CUDA kernels fn launches (empty where the profiler records none)
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    return {e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA}
+
+
+# 3-D grids with nx % 4 == 0: one ragged run (nx < 32), whole and ragged runs, short lines
+WIN_SHAPES = [
+    ((12, 5, 7), (0.2, 0.25, 0.3), 4),
+    ((20, 18, 10), (0.2, 0.2, 0.2), 0),
+    ((36, 7, 5), (0.25, 0.2, 0.3), 8),
+    ((64, 9, 11), (0.2, 0.3, 0.25), 0),
+]
+
+
+@pytest.mark.parametrize("nb", [20, 40, 64, 100, 128])
+@pytest.mark.parametrize("shape", range(len(WIN_SHAPES)))
+def test_windowed_stencil_gram_matches_oracle(shape, nb):
+    # A == B (one device array, as in the L-step and S-step): 64-column and 128-column forms
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    dims, spacing, pad = WIN_SHAPES[shape]
+    A, _, inv_rho = _case(dims, spacing, nb, 1, seed=30 + nb + shape, lda_pad=pad)
+    n = inv_rho.shape[0]
+    Go = _oracle_gram(dims, spacing, A[:, :n].T.astype(np.float64), A[:, :n].T.astype(np.float64),
+                      inv_rho.astype(np.float64))
+    dev = torch.device("cuda", 0)
+    At = torch.tensor(A, device=dev).T[:n]
+    r = torch.tensor(inv_rho, device=dev)
+    out = {}
+
+    def run():
+        out["G"] = D.stencil_gram(dims, spacing, At, At, r, variant=2)
+
+    names = _kernel_names(run)
+    if names:
+        assert any("gram_win_kernel" in k for k in names), sorted(names)
+    G = out["G"].cpu().numpy()
+    scale = np.abs(Go).max()
+    assert np.abs(G - Go).max() <= 3e-6 * scale
+    for k in range(Go.shape[0]):
+        assert np.linalg.norm(G[k] - Go[k]) <= 2e-6 * np.linalg.norm(Go[k])
+
+
+@pytest.mark.parametrize("nb", [64, 128])
+def test_windowed_stencil_gram_full_size_64cube(nb):
+    # 262,144 cells, the r x r and 2r x 2r widths of the solver's Grams, A == B: against the
+    # oracle and against the first tensor-core kernel. Both keep a block's partial sums in FP32
+    # in tensor memory over ~5,000 cells, i.e. ~1,900 MMA roundings per entry; the tensor core's
+    # FP32 accumulation rounds toward zero, so a same-sign sum (the diagonal, dominated by the
+    # -3 v0 term of the one-sided stencils on random data) shrinks by up to that many units in
+    # the last place: expected ~N 2^-25 = 6e-5, at most N 2^-23 = 2.3e-4 of the entry
+    import torch
+    from paper_2508_04484_gb300 import dlra as D
+    dims, spacing = (64, 64, 64), (0.2, 0.2, 0.2)
+    A, _, inv_rho = _case(dims, spacing, nb, 1, seed=7 + nb)
+    Go = _oracle_gram(dims, spacing, A.T.astype(np.float64), A.T.astype(np.float64), inv_rho.astype(np.float64))
+    dev = torch.device("cuda", 0)
+    At = torch.tensor(A, device=dev).T
+    r = torch.tensor(inv_rho, device=dev)
+    G = {v: D.stencil_gram(dims, spacing, At, At, r, variant=v).cpu().numpy() for v in (0, 1, 2)}
+    err = {v: max(np.linalg.norm(G[v][k] - Go[k]) / np.linalg.norm(Go[k]) for k in range(Go.shape[0]))
+           for v in G}
+    print(f"64^3, {nb} columns, A == B: relative error of the FMA / tensor-core / windowed Grams "
+          f"{err[0]:.2e} / {err[1]:.2e} / {err[2]:.2e}")
+    assert err[0] <= 2e-5
+    assert err[1] <= 2.3e-4 and err[2] <= 2.3e-4
