@@ -7,8 +7,9 @@ between replays, so it is run on a case a few GB in size whose buffers still exc
       one energy step of a 96^3 three-material phantom (1.5 mm, P_21, rank 60 state, the
       128^3 workload's voxels, physics and rank capacity) with a chosen streaming-stage
       kernel (0 per-cell FMA, 3 cell pairs, 4 / 5 / 6 TMA-staged tensor cores);
-  python -m paper_2508_04484_gb300.profile_case gram --variant 1
-      the same step with a chosen stencil-Gram kernel (0 FMA, 1 tensor cores).
+  python -m paper_2508_04484_gb300.profile_case gram --variant 2
+      the same step with a chosen stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores
+      with the sliding TMA window); the step launches it twice (r x r and 2r x 2r).
 
 Seeded synthetic inputs (workloads.ellipsoid_phantom, random orthonormal factors with
 decaying singular values); prints the rank log of the step.

@@ -154,20 +154,24 @@ def test_windowed_stencil_gram_matches_oracle(shape, nb):
     if names:
         assert any("gram_win_kernel" in k for k in names), sorted(names)
     G = out["G"].cpu().numpy()
+    # each tensor-core sum runs over at most 8 chunks x 12 MMAs = 96 roundings toward zero:
+    # a same-sign sum (the diagonal) may lose up to 96 x 2^-24 = 5.7e-6 of itself
     scale = np.abs(Go).max()
-    assert np.abs(G - Go).max() <= 3e-6 * scale
+    assert np.abs(G - Go).max() <= 6e-6 * scale
     for k in range(Go.shape[0]):
-        assert np.linalg.norm(G[k] - Go[k]) <= 2e-6 * np.linalg.norm(Go[k])
+        assert np.linalg.norm(G[k] - Go[k]) <= 6e-6 * np.linalg.norm(Go[k])
 
 
 @pytest.mark.parametrize("nb", [64, 128])
 def test_windowed_stencil_gram_full_size_64cube(nb):
-    # 262,144 cells, the r x r and 2r x 2r widths of the solver's Grams, A == B: against the
-    # oracle and against the first tensor-core kernel. Both keep a block's partial sums in FP32
-    # in tensor memory over ~5,000 cells, i.e. ~1,900 MMA roundings per entry; the tensor core's
-    # FP32 accumulation rounds toward zero, so a same-sign sum (the diagonal, dominated by the
-    # -3 v0 term of the one-sided stencils on random data) shrinks by up to that many units in
-    # the last place: expected ~N 2^-25 = 6e-5, at most N 2^-23 = 2.3e-4 of the entry
+    # 262,144 cells, the r x r and 2r x 2r widths of the solver's Grams, A == B: the three
+    # kernels against the oracle. The first tensor-core kernel keeps a block's partial sums in
+    # FP32 in tensor memory over ~3,500 cells, i.e. ~1,300 MMA roundings per entry; the tensor
+    # core's FP32 accumulation rounds toward zero, so a same-sign sum (the diagonal, dominated by
+    # the -3 v0 term of the one-sided stencils on random data) shrinks by up to that many units
+    # in the last place: expected ~N 2^-25 = 4e-5, at most N 2^-23 = 1.6e-4 (bound 2.3e-4). The
+    # windowed kernel restarts its tensor-core sums every 8 chunks (96 roundings, < 1.2e-5) and
+    # adds them with round-to-nearest FP32 additions
     import torch
     from paper_2508_04484_gb300 import dlra as D
     dims, spacing = (64, 64, 64), (0.2, 0.2, 0.2)
@@ -182,4 +186,5 @@ def test_windowed_stencil_gram_full_size_64cube(nb):
     print(f"64^3, {nb} columns, A == B: relative error of the FMA / tensor-core / windowed Grams "
           f"{err[0]:.2e} / {err[1]:.2e} / {err[2]:.2e}")
     assert err[0] <= 2e-5
-    assert err[1] <= 2.3e-4 and err[2] <= 2.3e-4
+    assert err[1] <= 2.3e-4
+    assert err[2] <= 1.2e-5
