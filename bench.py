@@ -62,11 +62,16 @@ def _args():
                    help="skip the batched-against-plain comparison on the 64^3 eight-beam phantom")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
-    p.add_argument("--stage-kernel", type=int, choices=[0, 1, 2, 3, 4, 5, 6, 7], default=None,
+    p.add_argument("--stage-kernel", type=int, choices=list(range(10)), default=None,
                    help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs, "
-                        "4 / 5 TMA-staged tensor cores, 128 / 256-cell bricks), set after the autotuner")
-    p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1], default=None,
-                   help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores), set after the autotuner")
+                        "4 / 5 TMA-staged tensor cores, 128 / 256-cell bricks, 6 persistent, 7 A in TMEM, "
+                        "8 2-CTA clusters, 9 three tiles along z), set after the autotuner")
+    p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1, 2], default=None,
+                   help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores with a TMA window), "
+                        "set after the autotuner")
+    p.add_argument("--apply-kernel", type=int, choices=[0, 1, 2], default=None,
+                   help="profiling: tall-skinny products (0 FMA, 1 tensor cores from 65,536 rows, 2 always), "
+                        "set after the autotuner")
     p.add_argument("--replicas", action="store_true",
                    help="with several ranks, solve the whole multi-beam workload on every rank")
     p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
@@ -98,10 +103,15 @@ STAGE_KERNELS = {
         "}  // namespace dlra", "kstage_tma.cuh"),
     8: ("kstage_tmac_kernel", "template <int RM>\n__global__ void __launch_bounds__(192) kstage_tmac_kernel(",
         "}  // namespace dlra", "kstage_tmac.cuh"),
+    9: ("kstage_tmat_kernel", "template <int RM, int T>\n__global__ void __launch_bounds__(KsTmaT<RM, T>::THREADS, 1)",
+        "}  // namespace dlra", "kstage_tmat.cuh"),
 }
 STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
                "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7,
-               "TMA tensor cores cluster": 8}
+               "TMA tensor cores cluster": 8,
+               "TMA tensor cores 3 tiles": 9}
+GRAM_NAMES = {"FMA": 0, "tensor cores": 1, "tensor cores TMA window": 2}
+APPLY_NAMES = {"FMA": 0, "tensor cores": 1}
 
 
 def stage_source_sha256(variant):
@@ -504,6 +514,18 @@ def main():
         solver.set_stage_kernel(args.stage_kernel)
     if args.stencil_gram_kernel is not None:
         solver.set_stencil_gram_kernel(args.stencil_gram_kernel)
+    if args.apply_kernel is not None:
+        solver.set_apply_kernel(args.apply_kernel)
+    # the kernels the timed solver runs, applied again to the end-to-end solver (a user tunes once
+    # and sets the chosen kernels on later contexts)
+    chosen = {
+        "stage": args.stage_kernel if args.stage_kernel is not None else (
+            STAGE_NAMES.get(tuned["stage_variant"], 0) if tuned else None),
+        "stencil_gram": args.stencil_gram_kernel if args.stencil_gram_kernel is not None else (
+            GRAM_NAMES.get(tuned["stencil_gram_kernel"], 0) if tuned else None),
+        "apply": args.apply_kernel if args.apply_kernel is not None else (
+            APPLY_NAMES.get(tuned["apply_kernel"], 0) if tuned else None),
+    }
     use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
     solver.set_graphs(use_graphs)
     with torch.cuda.stream(stream):
@@ -594,7 +616,7 @@ def main():
               "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
               "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
               "counts": "per cell and launch (5r + 1) words and 2 nk r^2 + 6 nk r flops at the step's rank"}
-    if variant in (1, 4, 5, 6, 7):
+    if variant in (1, 4, 5, 6, 7, 8, 9):
         # the r x r mix on the tensor cores (kind::tf32, three products per FP32-accurate product):
         # the dense TF32 peak from the measured sustained bf16 GEMM rate x the nominal TF32/bf16 ratio
         bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
@@ -623,8 +645,13 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = D.Solver(cfg, mats, w_host, my_beams, stream=stream.cuda_stream)
-        if tuned:
-            s2.set_stage_kernel(variant)
+        if chosen["stage"] is not None:
+            s2.set_stage_kernel(chosen["stage"])
+        if chosen["stencil_gram"] is not None:
+            s2.set_stencil_gram_kernel(chosen["stencil_gram"])
+        if chosen["apply"] is not None:
+            s2.set_apply_kernel(chosen["apply"])
+        s2.set_graphs(use_graphs)
         s2.step(K)
         s2.dose(out=dose_host)
         e2e_s = time.perf_counter() - t0
@@ -632,7 +659,8 @@ def main():
         e2e = {"value": (1 if shard else ws) * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w_host.nbytes),
                "d2h_bytes_per_step": int(dose_host.nbytes),
                "includes": "context creation with angular tables, host->device mixture weights, ray trace, "
-                           "all energy steps, dose read back to host (one whole solve)"}
+                           "all energy steps, dose read back to host (one whole solve) with the kernels the "
+                           "timed solver runs"}
     second = None
     if rank == 0 and ws == 1 and not args.no_second and name == WORKLOAD:
         second = _second_line(args, stream)

@@ -230,14 +230,15 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel) and of the truncation apply (FMA or tensor cores). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 24 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 .. 8 as dlra_set_stage_kernel), Gram block
+ * synchronises; drops captured graphs. report (optional, 26 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 .. 9 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
  * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
  * of its form with A in tensor memory, ms of the truncation apply with FMA and on the tensor
- * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage
- * (-1 where not applicable). */
+ * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage,
+ * ms of the windowed stencil Gram, ms of the three-tile form of the stage (-1 where not
+ * applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -254,7 +255,9 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * the products, leaving shared memory to the halo and B, 8 variant 7 on clusters of two CTAs
  * owning y-adjacent bricks: one multicast TMA copy loads the pair's common halo box and one
  * multicast bulk copy the chunk's B image into both CTAs (variant 7 where the cluster launch is
- * refused). Same results up to rounding; dlra_autotune picks among them. */
+ * refused), 9 variant 7 on bricks of three 128-cell tiles stacked along z (8 x 4 x 12 cells, one
+ * block per SM) sharing one halo box and one B image per chunk. Same results up to rounding;
+ * dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Kernel of the cell-side tall-skinny products (the augmentation's projections and the
@@ -268,8 +271,13 @@ dlra_status dlra_set_apply_kernel(dlra_ctx* ctx, int32_t variant);
 /* Stencil-Gram kernel (the Galerkin blocks X^T D_k rho^-1 X of the L-step and S-step):
  * 0 FMA (default), 1 on the tensor cores (FP32-mixed path only: tcgen05.mma kind::tf32 with
  * high/low TF32 splits of both operands, FP32 accumulation in tensor memory, FP64 sums across
- * blocks; the FMA kernel on FP64 or for more than 128 columns). Same results up to rounding;
- * dlra_autotune picks between them. */
+ * blocks; the FMA kernel on FP64 or for more than 128 columns), 2 on the tensor cores with the
+ * inputs staged by TMA in a window that slides along each stencil's axis and the stencil
+ * operand in tensor memory (FP32-mixed path, 3-D grids, the same basis on both sides: the
+ * L-step and S-step Grams; kernel 1 otherwise); its tensor-core sums restart every 8 chunks of
+ * 32 cells and are added up in FP32 with round-to-nearest (the tensor core's own FP32
+ * accumulation rounds toward zero, which leaves kernel 1's long sums up to ~5e-4 low at 2M
+ * cells). Same results up to rounding; dlra_autotune picks among them. */
 dlra_status dlra_set_stencil_gram_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* enable = 1: on the FP32-mixed path, the streaming stage runs on the fifth-generation tensor
@@ -353,7 +361,8 @@ dlra_status dlra_kstep_noalloc(const dlra_kstep_args* args);
  *   inv_rho : FP32, n values 1/rho_s(x);
  *   out: FP64, nk nb na values, G_k[a][b] at out[(k nb + b) na + a]; overwritten.
  * nk and k = 2 da + s as for dlra_kstep_args.P; 1 <= na, nb <= 128. variant: 0 FMA kernel,
- * 1 tensor-core kernel (as dlra_set_stencil_gram_kernel). */
+ * 1 tensor-core kernel, 2 windowed tensor-core kernel where A and B are the same array (as
+ * dlra_set_stencil_gram_kernel). */
 typedef struct {
   int32_t nx, ny, nz;
   double dx, dy, dz;
