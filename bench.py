@@ -69,6 +69,8 @@ def _args():
     p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1, 2], default=None,
                    help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores with a TMA window), "
                         "set after the autotuner")
+    p.add_argument("--gram-kernel", type=int, choices=[0, 1], default=None,
+                   help="profiling: tall-skinny Grams (0 FMA, 1 tensor cores), set after the autotuner")
     p.add_argument("--apply-kernel", type=int, choices=[0, 1, 2], default=None,
                    help="profiling: tall-skinny products (0 FMA, 1 tensor cores from 65,536 rows, 2 always), "
                         "set after the autotuner")
@@ -516,6 +518,8 @@ def main():
         solver.set_stencil_gram_kernel(args.stencil_gram_kernel)
     if args.apply_kernel is not None:
         solver.set_apply_kernel(args.apply_kernel)
+    if args.gram_kernel is not None:
+        solver.set_gram_kernel(args.gram_kernel)
     # the kernels the timed solver runs, applied again to the end-to-end solver (a user tunes once
     # and sets the chosen kernels on later contexts)
     chosen = {
@@ -525,6 +529,8 @@ def main():
             GRAM_NAMES.get(tuned["stencil_gram_kernel"], 0) if tuned else None),
         "apply": args.apply_kernel if args.apply_kernel is not None else (
             APPLY_NAMES.get(tuned["apply_kernel"], 0) if tuned else None),
+        "gram": args.gram_kernel if args.gram_kernel is not None else (
+            APPLY_NAMES.get(tuned["gram_kernel"], 0) if tuned else None),
     }
     use_graphs = args.graphs == "on" or (args.graphs == "auto" and len(beams) > 1)
     solver.set_graphs(use_graphs)
@@ -651,6 +657,8 @@ def main():
             s2.set_stencil_gram_kernel(chosen["stencil_gram"])
         if chosen["apply"] is not None:
             s2.set_apply_kernel(chosen["apply"])
+        if chosen["gram"] is not None:
+            s2.set_gram_kernel(chosen["gram"])
         s2.set_graphs(use_graphs)
         s2.step(K)
         s2.dose(out=dose_host)

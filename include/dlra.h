@@ -230,15 +230,15 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel) and of the truncation apply (FMA or tensor cores). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 26 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * synchronises; drops captured graphs. report (optional, 27 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
  * stencil-Gram grids, the chosen stage variant (0 .. 9 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
  * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
  * of its form with A in tensor memory, ms of the truncation apply with FMA and on the tensor
  * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage,
- * ms of the windowed stencil Gram, ms of the three-tile form of the stage (-1 where not
- * applicable). */
+ * ms of the windowed stencil Gram, ms of the three-tile form of the stage, ms of the Gram
+ * reduction on the tensor cores (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -259,6 +259,16 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * block per SM) sharing one halo box and one B image per chunk. Same results up to rounding;
  * dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
+
+/* Kernel of the cell-side tall-skinny Grams (the augmentation's projections X^T K and the
+ * Grams of its pivoted CholeskyQR2 passes, Sec. 2.2; the material Grams X^T diag(w_k) X of the
+ * collided scattering step, Sec. 3.3.1): 0 FMA with FP64 sums across blocks (default), 1 on the
+ * tensor cores (FP32 path, at least 65,536 cells and 8 columns, at most 128 columns on the
+ * X side: 32-row chunks loaded by TMA, TF32 high/low splits, tcgen05.mma kind::tf32, sums
+ * restarted every 8 chunks and added up in FP32 with round-to-nearest, FP64 across blocks; the
+ * FMA kernel otherwise), 2 as 1 at any cell count. Same results up to rounding; dlra_autotune
+ * picks between 0 and 1. */
+dlra_status dlra_set_gram_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Kernel of the cell-side tall-skinny products (the augmentation's projections and the
  * truncation's X = X^ P, Sec. 2.2): 0 one thread per cell with FMA (default), 1 on the tensor

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "small.cu", "raytrace.cu", "adjoint.cu", "gram_tc.cu", "gram_win.cu", "noalloc.cu",
+SOURCES = ["capi.cu", "small.cu", "raytrace.cu", "adjoint.cu", "gram_tc.cu", "gram_win.cu", "gram_tt.cu", "noalloc.cu",
            "straggling.cu", "tables.cpp", "straggling_tables.cpp"]
 HEADERS = ["device.cuh", "kernels.h", "tables.h", "tcgen05.cuh", "kstage_tc.cuh", "kstage_tma.cuh", "kstage_tmac.cuh",
            "apply_tc.cuh", "straggling_march.cuh"]

@@ -222,6 +222,9 @@ struct Tuning {
                               // 128-cell tiles along z
   int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path), 2 tcgen05 with a TMA window (A == B, 3-D)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
+  int gram_variant = 0;       // tall-skinny Grams: 0 FMA, 1 tcgen05 (FP32 path, tall, at least 8 columns),
+                              // 2 tcgen05 at any height
+  int* gram_err = nullptr;    // error word of the tensor-core Grams (the context's)
   int apply_variant = 0;      // tall-skinny applies: 0 FMA, 1 tcgen05 (FP32 path, tall, 16 <= N, Q <= 128),
                               // 2 tcgen05 at any height
 };
@@ -262,6 +265,23 @@ template <typename T, class F>
 void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int* adim, int acap, int ncols_j, F f,
           double* out, long long ldo, int64_t& nl) {
   if (rows <= 0 || acap <= 0 || ncols_j <= 0) return;
+  // on the tensor cores (FP32 path, tall, at least 8 F columns; the narrow reductions stay below)
+  if constexpr (std::is_same<T, float>::value) {
+    const int gv = tuning().gram_variant;
+    if (((gv == 1 && rows >= 65536) || gv == 2) && ncols_j >= 8) {
+      bool done = false;
+      if constexpr (std::is_same<F, FPlain<T>>::value)
+        done = launch_gram_tt(st, rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j, nullptr, 0, 1, out, ldo,
+                              tuning().gram_err);
+      if constexpr (std::is_same<F, FDiag<T>>::value)
+        done = launch_gram_tt(st, rows, A, lda, adim, acap, f.B, f.ldb, f.bdim, f.nb, ncols_j, f.wv, f.nb, f.nk, out,
+                              ldo, tuning().gram_err);
+      if (done) {
+        ++nl;
+        return;
+      }
+    }
+  }
   if constexpr (std::is_same<F, FPlain<T>>::value) {
     if (ncols_j <= 2 && rows >= 4096) {
       // a few columns (the source step's rank-M updates): a bandwidth-bound reduction
@@ -1437,6 +1457,7 @@ dlra_status alloc_shared(dlra_ctx* ctx) {
   ALLOC(ctx->tau_cell, sizeof(double) * n);
   ALLOC(ctx->Apm, sizeof(T) * (size_t)nk * m * m);
   ALLOC(ctx->dev_err, sizeof(int));
+  ctx->tun.gram_err = ctx->dev_err;
   ALLOC(ctx->flags_dev, sizeof(int) * ctx->K);
   ALLOC(ctx->dose_tmp, sizeof(double) * n);
   ALLOC(ctx->zeros, sizeof(double) * n);
@@ -2255,7 +2276,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[26] = {0};
+  double rep[27] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
   // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
   // nx % 4 == 0, rank capacity >= 32)
@@ -2302,6 +2323,17 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
               n2, nl);
     });
   }
+  // the same Gram on the tensor cores (FP32 path)
+  double gram_tc_ms = -1.0;
+  if (sizeof(T) == 4 && n >= 65536) {
+    t.gram_blocks = gb[0];
+    t.gram_variant = 1;
+    gram_tc_ms = time_ms([&] {
+      gram<T>(st, n, E.P(L.Xh), n, nullptr, n2, RB, FPlain<T>{E.P(L.Xh) + (long long)RB * n, n, nullptr, RB}, L.Cg,
+              n2, nl);
+    });
+    t.gram_variant = 0;
+  }
   // stencil Gram on the augmented basis
   const int gw[3] = {1, 2, 4};
   for (int v = 0; v < 3; ++v) {
@@ -2342,6 +2374,8 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   for (int v = 1; v < 4; ++v)
     if (rep[2 + v] < rep[2 + bi]) bi = v;
   best.gram_blocks = gb[bi];
+  best.gram_variant = (gram_tc_ms > 0.0 && gram_tc_ms < rep[2 + bi]) ? 1 : 0;
+  rep[26] = gram_tc_ms;
   int wi = 0;
   for (int v = 1; v < 3; ++v)
     if (rep[6 + v] < rep[6 + wi]) wi = v;
@@ -2807,6 +2841,16 @@ dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;
+  return DLRA_OK;
+}
+
+dlra_status dlra_set_gram_kernel(dlra_ctx* ctx, int32_t variant) {
+  if (!ctx) return DLRA_ERR_ARG;
+  if (ctx->poisoned) return ctx->poisoned;
+  if (variant < 0 || variant > 2) return fail(ctx, DLRA_ERR_ARG, "Gram kernel variant must be 0, 1 or 2");
+  CK(cudaStreamSynchronize(ctx->st));
+  drop_graphs(ctx);
+  ctx->tun.gram_variant = variant;
   return DLRA_OK;
 }
 

@@ -173,6 +173,15 @@ void launch_gram_stencil_tc(cudaStream_t st, long long rows, const float* A, lon
 bool launch_gram_stencil_win(cudaStream_t st, long long rows, const float* A, long long lda, int na,
                              const int* adim, const float* B, long long ldb, int nb, const int* bdim,
                              const float* inv_rho, const Geo& g, double* out, int ldj, long long ldo, int* err);
+// Tall-skinny Gram on the tensor cores (gram_tt.cu): out[j ldo + a] += sum_t A(t, a) F(t, j) for
+// a < dim(adim, acap), j < ncols, with F(t, j) = B(t, j) (nbw == 0, j < dim(jdim, jcap)) or
+// F(t, k nbw + b) = wv[k rows + t] B(t, b) (k < nk, b < dim(jdim, jcap)). Needs acap <= 128,
+// rows < 2^31, lda, ldb multiples of 4 and 16-byte aligned bases (and nbw <= 64, nk <= 8 for
+// the weighted form); returns false (nothing launched) otherwise. A wait that runs out sets
+// ERR_TIMEOUT in *err and leaves out without this launch's terms.
+bool launch_gram_tt(cudaStream_t st, long long rows, const float* A, long long lda, const int* adim, int acap,
+                    const float* B, long long ldb, const int* jdim, int jcap, int ncols, const float* wv, int nbw,
+                    int nk, double* out, long long ldo, int* err);
 // cuTensorMapEncodeTiled from the driver (nullptr where it cannot be had)
 PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn();
 

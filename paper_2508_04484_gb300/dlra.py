@@ -112,6 +112,7 @@ SIGNATURES = {
     "dlra_backward": ([_P, _P, C.c_int32, _DP, _P, C.c_int32], C.c_int),
     "dlra_autotune": ([_P, _DP], C.c_int),
     "dlra_set_stage_kernel": ([_P, C.c_int32], C.c_int),
+    "dlra_set_gram_kernel": ([_P, C.c_int32], C.c_int),
     "dlra_set_tensor_cores": ([_P, C.c_int32], C.c_int),
     "dlra_set_graphs": ([_P, C.c_int32], C.c_int),
     "dlra_set_adjoint_store": ([_P, C.c_int32], C.c_int),
@@ -357,7 +358,7 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(26)
+    rep = np.zeros(27)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
@@ -371,7 +372,8 @@ def dlra_autotune(ctx):
                                "TMA tensor cores A in TMEM", "TMA tensor cores cluster",
                                "TMA tensor cores 3 tiles")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
-                stencil_gram_window_ms=rep[24],
+                stencil_gram_window_ms=rep[24], gram_tensor_core_ms=rep[26],
+                gram_kernel="tensor cores" if 0.0 < rep[26] < min(rep[2:6]) else "FMA",
                 stencil_gram_kernel=("FMA", "tensor cores", "tensor cores TMA window")[int(rep[14])])
 
 
@@ -393,6 +395,10 @@ def dlra_set_graphs(ctx, enable=True):
 
 def dlra_set_straggling(ctx, enable=True, n_elem=128, h_max=0.01, straggling=True):
     _check(ctx, load().dlra_set_straggling(ctx, 1 if enable else 0, int(n_elem), float(h_max), 1 if straggling else 0))
+
+
+def dlra_set_gram_kernel(ctx, variant: int):
+    _check(ctx, load().dlra_set_gram_kernel(ctx, int(variant)))
 
 
 def dlra_set_apply_kernel(ctx, variant: int):
@@ -635,6 +641,10 @@ class Solver:
         dlra_set_straggling(self.ctx, enable, n_elem, h_max, straggling)
         if self.beam_ids:
             self.reset(retrace=True)
+
+    def set_gram_kernel(self, variant):
+        """0 FMA, 1 tensor cores for the cell-side tall-skinny Grams (FP32 path, tall), 2 tensor cores always."""
+        dlra_set_gram_kernel(self.ctx, variant)
 
     def set_apply_kernel(self, variant):
         """0 FMA, 1 tensor cores for the cell-side tall-skinny products (FP32 path)."""

@@ -222,3 +222,30 @@ def test_windowed_stencil_gram_in_solver(case):
     print(f"windowed stencil Gram on {case}: against the FMA Grams {e_fma:.2e}, against the oracle {e_or:.2e}")
     assert 0.0 < e_fma < 1e-5
     assert e_or < 1e-3
+
+
+@pytest.mark.parametrize("case", ["ragged", "phantom_128cube"])
+def test_tensor_core_grams_in_solver(case):
+    # the cell-side tall-skinny Grams on the tensor cores, forced at every height (Gram kernel 2):
+    # the augmentation's X^T K (B its own array), the CholeskyQR2 Grams (B a column block of X^),
+    # the material Grams X^T diag(w_k) X (weighted; at capacity 40 a slice of 64 columns spans
+    # two materials), on a ragged last chunk and at the phantom widths: against the FMA Grams
+    # and the oracle
+    if case == "ragged":
+        cfg, mats, w, beams, prob, (X, S, W), st, log = _ragged_instance()
+    else:
+        cfg, mats, w, beams, r, mode, kw = _instance(case, WL.FP32_MIXED)
+        prob, src, (X, S, W), st, log, _ = _oracle_run(case)
+    us = []
+    for v in (0, 2):
+        s = gpu_solver(cfg, mats, w, beams, schedule=np.asarray(log, dtype=np.int32), precision=WL.FP32_MIXED)
+        s.set_gram_kernel(v)
+        s.set_state(X, S, W)
+        s.step(prob.K)
+        Xg, Sg, Wg = s.get_state()
+        us.append(Xg @ Sg @ Wg.T)
+        s.close()
+    e_fma, e_or = rel_l2(us[1], us[0]), rel_l2(us[1], st.u())
+    print(f"tensor-core Grams on {case}: against the FMA Grams {e_fma:.2e}, against the oracle {e_or:.2e}")
+    assert 0.0 < e_fma < 1e-5
+    assert e_or < 1e-3
