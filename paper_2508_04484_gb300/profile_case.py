@@ -9,7 +9,8 @@ between replays, so it is run on a case a few GB in size whose buffers still exc
       kernel (0 per-cell FMA, 3 cell pairs, 4 / 5 / 6 TMA-staged tensor cores);
   python -m paper_2508_04484_gb300.profile_case gram --variant 2
       the same step with a chosen stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores
-      with the sliding TMA window); the step launches it twice (r x r and 2r x 2r).
+      with the sliding TMA window); the step launches it twice (r x r and 2r x 2r);
+  --gram-kernel 1 runs the step's tall-skinny Grams on the tensor cores (gram_tt_kernel).
 
 Seeded synthetic inputs (workloads.ellipsoid_phantom, random orthonormal factors with
 decaying singular values); prints the rank log of the step.
@@ -26,6 +27,7 @@ def main(argv=None):
     p.add_argument("case", choices=["stage", "gram"])
     p.add_argument("--variant", type=int, default=4)
     p.add_argument("--edge", type=int, default=96)
+    p.add_argument("--gram-kernel", type=int, default=0, help="tall-skinny Grams: 0 FMA, 1 tensor cores")
     a = p.parse_args(argv)
     import torch
 
@@ -56,6 +58,7 @@ def main(argv=None):
     else:
         s.set_stage_kernel(4)
         s.set_stencil_gram_kernel(a.variant)
+    s.set_gram_kernel(a.gram_kernel)
     s.step(1)
     torch.cuda.synchronize()
     print("rank log of the step:", s.rank_log()[0].tolist())
