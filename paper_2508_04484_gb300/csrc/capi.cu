@@ -261,6 +261,17 @@ void gemm(cudaStream_t st, long long rows, int N, int Q, AL al, BL bl, EP ep, in
   ++nl;
 }
 
+// m-side RK4 stage of the L-step (Sec. 2.2, the L equation): out = y + beta sum_k A_k z G_k^T
+// (A_k row-major m x m, G_k[c][a] at GT[(k RB + c) RB + a]; columns beyond the rank stay y)
+template <typename T>
+void lstage(cudaStream_t st, int m, int nk, int RB, const int* rdim, const T* Apm, const T* z, const T* y, T* out,
+            const T* GT, T* U, T beta, int64_t& nl) {
+  gemm<T, 16>(st, (long long)nk * m, RB, m, ALoadRowMajor<T>{Apm, m, m}, BLoadCol<T, T>{z, m, nullptr, m, rdim, RB},
+              EpiStoreKBlocks<T>{U, m, RB}, nl);
+  gemm<T, 16>(st, m, RB, nk * RB, ALoadPlain<T>{U, m, nullptr, nk * RB}, BLoadGt<T>{GT, RB, nk, rdim},
+              EpiKStage<T>{out, y, m, beta}, nl);
+}
+
 template <typename T, class F>
 void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int* adim, int acap, int ncols_j, F f,
           double* out, long long ldo, int64_t& nl) {
@@ -756,6 +767,7 @@ struct Lane {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   void *Kb[3] = {nullptr, nullptr, nullptr}, *Xh = nullptr, *Asrc = nullptr;
   void *Lb[3] = {nullptr, nullptr, nullptr}, *Zm = nullptr, *Wh = nullptr, *L1T = nullptr, *Pst = nullptr;
+  void* Ul = nullptr;  // L-step stages: U_k = A_k z, nk blocks of m x RB
   void* GtT = nullptr;
   double *G1 = nullptr, *Gc = nullptr, *Ph = nullptr, *P1 = nullptr, *C1 = nullptr, *Cg = nullptr, *Mapply = nullptr;
   double *Sh = nullptr, *Pt = nullptr, *Qt = nullptr, *Mg = nullptr, *XA = nullptr;
@@ -1158,10 +1170,6 @@ struct Engine {
     // RK4 Horner stages: K-step on st, L-step on sm
     const int ns = ctx->nsub[k];
     const double hs = ctx->h / ns;
-    const size_t lsmem =
-        ((size_t)nk * m + (size_t)nk * RB * RB + (size_t)(128 / (RB <= 32 ? 32 : 64)) * nk * RB) * sizeof(T);
-    if (lsmem > 48 * 1024)
-      cudaFuncSetAttribute(lstage_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
     for (int jj = 0; jj < ns; ++jj) {
       // the transposed K-step runs the sub-steps backwards (their adjoints pair with the
       // forward stages of the same sub-step); the polynomials of one energy step commute,
@@ -1194,9 +1202,9 @@ struct Engine {
         prof_end(ctx, st);
         double lbeta[4];
         horner_betas(ctx, ctx->E[k] - jj * hs, hs, lbeta);
-        lstage_kernel<T><<<m, 128, lsmem, sm>>>(P(ctx->Apm), m, nk, lin, ly, louts[s2], P(L->GtT), RB, rdim,
-                                                 T(lbeta[s2]));
-        ++nl;
+        // the m-side stage out = y + beta sum_k A_k z G_k^T as two tiled products: U_k = A_k z
+        // for all k at once (nk m x m by m x r), then y + beta [U_0 .. U_nk-1] [G_0^T; ..]
+        lstage<T>(sm, m, nk, RB, rdim, P(ctx->Apm), lin, ly, louts[s2], P(L->GtT), P(L->Ul), T(lbeta[s2]), nl);
         lin = louts[s2];
       }
     }
@@ -1481,6 +1489,7 @@ dlra_status alloc_lane(dlra_ctx* ctx) {
   ALLOC(L.Zm, sizeof(T) * (size_t)m * nk * n2);
   ALLOC(L.Wh, sizeof(T) * (size_t)m * n2);
   ALLOC(L.L1T, sizeof(T) * (size_t)m * RB);
+  ALLOC(L.Ul, sizeof(T) * (size_t)nk * RB * m);
   ALLOC(L.Pst, sizeof(T) * (size_t)nk * RB * RB);
   ALLOC(L.GtT, sizeof(T) * (size_t)nk * RB * RB);
   ALLOC(L.G1, sizeof(double) * nk * RB * RB);

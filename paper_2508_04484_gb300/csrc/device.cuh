@@ -290,6 +290,24 @@ struct BLoadKBlocks {
   }
 };
 
+// B producer for the L-step's sum over k: B((k, a), c) = G_k[c][a] = GT[(k * RB + c) * RB + a],
+// zero for a, c >= rdim (the columns beyond the rank).
+template <typename T>
+struct BLoadGt {
+  const T* GT;
+  int RB, nk;
+  const int* rdim;
+  __device__ void load(T* sB, int BK, int BN, int q0, int c0) const {
+    const int r = dev_dim(rdim, RB);
+    for (int e = threadIdx.x; e < BK * BN; e += blockDim.x) {
+      int kk = e % BK, c = e / BK;
+      int q = q0 + kk, cc = c0 + c;
+      int k = q / RB, a = q - k * RB;
+      sB[kk * BN + c] = (k < nk && a < r && cc < r) ? GT[((long long)k * RB + cc) * RB + a] : T(0);
+    }
+  }
+};
+
 // Epilogues. Each receives the accumulator of C(r, c) = sum_q A(r, q) B(q, c).
 template <typename T>
 struct EpiStore {  // C = acc (+ beta * Cin)
@@ -945,69 +963,6 @@ __global__ void __launch_bounds__(512) gram_stencil_kernel(long long rows, const
       double val = (double)acc[u][v];
       if (val != 0.0) atomicAdd(out + ((long long)k * ldj + b) * ldo + a, val);
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// m-side RK4 stage of the L-step: out = y + beta * sum_k Apm_k z G_k^T
-// (Apm_k = A^s_d row-major m x m, G_k at G[(k*RB + b)*RB + a] = G_k[a][b]).
-// Each block owns LS_RPB rows: V_k = Apm_k(rows, :) z, acc += V_k G_k^T.
-// ---------------------------------------------------------------------------
-// One block per moment row p. The rows p of the nk operators and the G_k (as T,
-// GT[(k*RB + c)*RB + a] = G_k[c][a]) are staged in shared memory; thread (a, g)
-// forms the partial dot products V_k(a) = sum_q Apm_k[p][q] z(q, a) over its
-// quarter (or half) of q, then out(p, c) = y(p, c) + beta sum_k sum_a V_k(a) G_k[c][a].
-template <typename T>
-__global__ void __launch_bounds__(128) lstage_kernel(const T* __restrict__ Apm, int m, int nk,
-                                                     const T* __restrict__ z, const T* __restrict__ y,
-                                                     T* __restrict__ out, const T* __restrict__ GT, int RB,
-                                                     const int* __restrict__ rdim, T beta) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  T* sA = reinterpret_cast<T*>(raw);     // nk x m
-  T* sG = sA + nk * m;                   // nk x RB x RB
-  T* sP = sG + nk * RB * RB;             // groups x nk x RB partial sums
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int r = dev_dim(rdim, RB);
-  const int p = blockIdx.x;
-  for (int e = tid; e < nk * m; e += nt) {
-    const int k = e / m, q = e - k * m;
-    sA[e] = Apm[((long long)k * m + p) * m + q];
-  }
-  for (int e = tid; e < nk * RB * RB; e += nt) sG[e] = GT[e];
-  __syncthreads();
-  const int aw = RB <= 32 ? 32 : 64;
-  const int groups = nt / aw;
-  const int a = tid % aw, g = tid / aw;
-  const int q0 = (m * g) / groups, q1 = (m * (g + 1)) / groups;
-  if (a < r) {
-    T part[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    const T* za = z + (long long)a * m;
-#pragma unroll 4
-    for (int q = q0; q < q1; ++q) {
-      const T zv = za[q];
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k < nk) part[k] += sA[k * m + q] * zv;
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (k < nk) sP[(g * nk + k) * RB + a] = part[k];
-  } else if (a < RB) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (k < nk) sP[(g * nk + k) * RB + a] = T(0);
-  }
-  __syncthreads();
-  for (int c = tid; c < RB; c += nt) {
-    T acc = T(0);
-    if (c < r)
-      for (int k = 0; k < nk; ++k)
-        for (int aa = 0; aa < r; ++aa) {
-          T v = T(0);
-          for (int gg = 0; gg < groups; ++gg) v += sP[(gg * nk + k) * RB + aa];
-          acc += v * sG[(k * RB + c) * RB + aa];
-        }
-    out[(long long)c * m + p] = y[(long long)c * m + p] + beta * acc;
   }
 }
 
