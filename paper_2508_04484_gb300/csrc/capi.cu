@@ -650,7 +650,10 @@ bool apply_tc_launch(cudaStream_t st, long long rows, const float* A, long long 
   float* img = reinterpret_cast<float*>(tcw.img);
   apply_tc_bimg_kernel<NP><<<nblk((long long)NP * Cf::QMAX, 256), 256, 0, st>>>(M, ldm, Q, qdim, N, img);
   cudaFuncSetAttribute(apply_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
-  apply_tc_kernel<NP><<<(unsigned)((rows + 127) / 128), Cf::THREADS, Cf::SMEM, st>>>(
+  // persistent: two blocks per SM over the 128-row tiles
+  const long long tiles = (rows + 127) / 128;
+  const unsigned grid = (unsigned)std::max(1LL, std::min(tiles, 2LL * device_sms()));
+  apply_tc_kernel<NP><<<grid, Cf::THREADS, Cf::SMEM, st>>>(
       m, rows, Q, qdim, img, N, C, ldc, Cin, alpha, beta, V, inv_rho, tcw.err);
   return true;
 }
