@@ -294,18 +294,20 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
     }
   }
   if constexpr (std::is_same<F, FPlain<T>>::value) {
-    if (ncols_j <= 2 && rows >= 4096) {
+    if (ncols_j <= 4 && rows >= 4096) {
       // a few columns (the source step's rank-M updates): a bandwidth-bound reduction
       // at least eight rows per thread: the block reduction at the end costs ~5 x 32 shuffles
       const unsigned gx =
           (unsigned)std::max<long long>(1, std::min<long long>((rows + 2047) / 2048, 2LL * device_sms()));
       const dim3 grid(gx, (unsigned)((acap + 31) / 32));
-      if (ncols_j == 1)
-        gram_narrow_kernel<T, 1><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j,
-                                                       out, ldo);
-      else
-        gram_narrow_kernel<T, 2><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j,
-                                                       out, ldo);
+#define NARROW(NC)                                                                                                 \
+  gram_narrow_kernel<T, NC><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j, out, \
+                                                  ldo)
+      if (ncols_j == 1) NARROW(1);
+      else if (ncols_j == 2) NARROW(2);
+      else if (ncols_j == 3) NARROW(3);
+      else NARROW(4);
+#undef NARROW
       ++nl;
       return;
     }

@@ -44,7 +44,7 @@ __device__ T block_sum(T v, T* sbuf) {
 // pivoted-Cholesky factor of the projected Gram (CholeskyQR with pivoting)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restrict__ G, const double* __restrict__ C1, int RBa, int qcap,
-                                   double drop_tol, double* __restrict__ Mout, int* qout, int* err) {
+                                   double drop_tol, double* __restrict__ Mout, int* qout, int* err, int stage) {
   extern __shared__ double sh[];
   __shared__ double red[32];
   __shared__ double rdiag[128];          // 1 / L_ii
@@ -53,8 +53,14 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
   const int ldg = RBa + qcap;
   double* A = sh;                        // qcap x qcap, col-major A[j*qcap + i]
   double* Li = A + qcap * qcap;          // inverse of the lower factor
-  int* perm = reinterpret_cast<int*>(Li + qcap * qcap);
+  double* Gs = Li + qcap * qcap;         // the Gram G (ldg x qcap), staged where it fits
+  int* perm = reinterpret_cast<int*>(Gs + (stage ? (size_t)ldg * qcap : 0));
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (stage) {
+    for (int e = tid; e < ldg * qcap; e += nt) Gs[e] = G[e];
+    __syncthreads();
+    G = Gs;
+  }
   // G' = R^T R - C2^T C2 (C2 = Xa^T R is the top block)
   for (int e = tid; e < qcap * qcap; e += nt) {
     int i = e % qcap, j = e / qcap;
@@ -133,12 +139,19 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
   for (int i = tid; i < q; i += nt) rdiag[i] = 1.0 / A[i * qcap + i];
   for (int i = tid; i < qcap; i += nt) iperm[perm[i]] = i;
   __syncthreads();
-  // inverse of the lower factor L (q x q): column c solves L x = e_c
-  for (int c = tid; c < q; c += nt) {
+  // inverse of the lower factor L (q x q): column c solves L x = e_c, four lanes per column
+  // (the sums over k split four ways and combined by shuffles)
+  for (int c0 = tid >> 2; c0 < ((q + 63) / 64) * 64; c0 += nt >> 2) {
+    const int c = c0, part = tid & 3;
+    const bool act = c < q;
     for (int i = 0; i < q; ++i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) v -= A[k * qcap + i] * Li[c * qcap + k];
-      Li[c * qcap + i] = (i < c) ? 0.0 : v * rdiag[i];
+      double v = 0.0;
+      if (act)
+        for (int k = c + part; k < i; k += 4) v -= A[k * qcap + i] * Li[c * qcap + k];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (act && part == 0) Li[c * qcap + i] = (i < c) ? 0.0 : (v + (i == c ? 1.0 : 0.0)) * rdiag[i];
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -162,9 +175,12 @@ __global__ void __launch_bounds__(256) orth_factor_kernel(const double* __restri
 
 void launch_orth_factor(cudaStream_t st, const double* G, const double* C1, int RBa, int qcap, double drop_tol,
                         double* Mout, int* qout, int* err) {
-  size_t smem = (size_t)2 * qcap * qcap * sizeof(double) + (size_t)qcap * sizeof(int) + 16;
+  const size_t base = (size_t)2 * qcap * qcap * sizeof(double) + (size_t)qcap * sizeof(int) + 16;
+  const size_t staged = base + (size_t)(RBa + qcap) * qcap * sizeof(double);
+  const int stage = staged <= 200 * 1024 ? 1 : 0;
+  const size_t smem = stage ? staged : base;
   if (smem > 48 * 1024) cudaFuncSetAttribute(orth_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  orth_factor_kernel<<<1, 256, smem, st>>>(G, C1, RBa, qcap, drop_tol, Mout, qout, err);
+  orth_factor_kernel<<<1, 256, smem, st>>>(G, C1, RBa, qcap, drop_tol, Mout, qout, err, stage);
 }
 
 // ---------------------------------------------------------------------------
