@@ -294,7 +294,7 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
     }
   }
   if constexpr (std::is_same<F, FPlain<T>>::value) {
-    if (ncols_j <= 4 && rows >= 4096) {
+    if (ncols_j <= 2 && rows >= 4096) {
       // a few columns (the source step's rank-M updates): a bandwidth-bound reduction
       // at least eight rows per thread: the block reduction at the end costs ~5 x 32 shuffles
       const unsigned gx =
@@ -304,9 +304,7 @@ void gram(cudaStream_t st, long long rows, const T* A, long long lda, const int*
   gram_narrow_kernel<T, NC><<<grid, 256, 0, st>>>(rows, A, lda, adim, acap, f.B, f.ldb, f.jdim, f.jcap, ncols_j, out, \
                                                   ldo)
       if (ncols_j == 1) NARROW(1);
-      else if (ncols_j == 2) NARROW(2);
-      else if (ncols_j == 3) NARROW(3);
-      else NARROW(4);
+      else NARROW(2);
 #undef NARROW
       ++nl;
       return;
