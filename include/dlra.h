@@ -230,15 +230,16 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel) and of the truncation apply (FMA or tensor cores). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 27 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 .. 9 as dlra_set_stage_kernel), Gram block
+ * synchronises; drops captured graphs. report (optional, 28 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 .. 10 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
  * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
  * of its form with A in tensor memory, ms of the truncation apply with FMA and on the tensor
  * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage,
  * ms of the windowed stencil Gram, ms of the three-tile form of the stage, ms of the Gram
- * reduction on the tensor cores (-1 where not applicable). */
+ * reduction on the tensor cores, ms of the eight-column form of the stage (-1 where not
+ * applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -256,7 +257,8 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * owning y-adjacent bricks: one multicast TMA copy loads the pair's common halo box and one
  * multicast bulk copy the chunk's B image into both CTAs (variant 7 where the cluster launch is
  * refused), 9 variant 7 on bricks of three 128-cell tiles stacked along z (8 x 4 x 12 cells, one
- * block per SM) sharing one halo box and one B image per chunk. Same results up to rounding;
+ * block per SM) sharing one halo box and one B image per chunk, 10 variant 7 on chunks of eight
+ * input columns (half the chunks per brick). Same results up to rounding;
  * dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
