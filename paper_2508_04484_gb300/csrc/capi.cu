@@ -2460,12 +2460,15 @@ static int kstep_rank_cap(int r) {
   return -1;
 }
 
-size_t kstep_scratch_bytes(long long n, int r, int nact) {
+size_t kstep_scratch_bytes(long long n, int r, int nact, int stage_kernel) {
   const int RB = kstep_rank_cap(r);
   if (RB < 0) return 0;
   const size_t al = 256;
   auto up = [&](size_t b) { return (b + al - 1) / al * al; };
-  return 3 * up(sizeof(float) * (size_t)n * RB) + up(sizeof(float) * (size_t)2 * nact * RB * RB) + up(sizeof(int));
+  // the TMA-staged tensor-core stages read their B operand from images built per launch
+  const size_t bimg = (stage_kernel >= 4 && nact == 3) ? up(kstage_tma_bimg_bytes(RB)) : 0;
+  return 3 * up(sizeof(float) * (size_t)n * RB) + up(sizeof(float) * (size_t)2 * nact * RB * RB) + up(sizeof(int)) +
+         bimg;
 }
 
 int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, int msg_len) {
@@ -2474,7 +2477,7 @@ int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, 
   const int nact = two_d ? 2 : 3;
   const long long n = (long long)a.nx * a.ny * a.nz;
   const int RB = kstep_rank_cap(a.r);
-  const size_t need = kstep_scratch_bytes(n, a.r, nact);
+  const size_t need = kstep_scratch_bytes(n, a.r, nact, a.stage_kernel);
   if (scratch_bytes < need) {
     std::snprintf(msg, msg_len, "K-step needs %zu bytes of work space, %zu available", need, scratch_bytes);
     return DLRA_ERR_ARG;
@@ -2489,6 +2492,7 @@ int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, 
   float* Pst = reinterpret_cast<float*>(base + 3 * up(sizeof(float) * (size_t)n * RB));
   int* rdev = reinterpret_cast<int*>(base + 3 * up(sizeof(float) * (size_t)n * RB) +
                                      up(sizeof(float) * (size_t)2 * nact * RB * RB));
+  void* bimg = (a.stage_kernel >= 4 && nact == 3) ? reinterpret_cast<char*>(rdev) + up(sizeof(int)) : nullptr;
   Geo g{};
   g.nx = a.nx;
   g.ny = a.ny;
@@ -2514,7 +2518,7 @@ int run_kstep(const void* argp, void* scratch, size_t scratch_bytes, char* msg, 
     float* vouts[4] = {vb, va, vb, va};
     for (int s2 = 0; s2 < 4; ++s2)
       kstage<float>(RB, st, vins[s2], y, y, vouts[s2], n, a.inv_rho, g, Pst, rdev, (float)beta[s2], s2 == 3 ? 1 : 0,
-                    nl);
+                    nl, nullptr, a.stage_kernel, bimg);
   }
   kstep_store<<<nblk(n * a.r, 256), 256, 0, st>>>(y, n, a.r, a.K1);
   cudaError_t e = cudaGetLastError();
@@ -2535,8 +2539,9 @@ int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
     std::snprintf(msg, msg_len, "bad grid");
     return DLRA_ERR_ARG;
   }
-  if (a->r < 1 || a->r > 64 || a->n_sub < 1 || !(a->de > 0) || !(a->e0 - a->de > 0)) {
-    std::snprintf(msg, msg_len, "need 1 <= r <= 64, n_sub >= 1, e0 > de > 0");
+  if (a->r < 1 || a->r > 64 || a->n_sub < 1 || !(a->de > 0) || !(a->e0 - a->de > 0) || a->stage_kernel < 0 ||
+      a->stage_kernel > 10) {
+    std::snprintf(msg, msg_len, "need 1 <= r <= 64, n_sub >= 1, e0 > de > 0, stage kernel 0 .. 10");
     return DLRA_ERR_ARG;
   }
   if (!a->K0 || !a->K1 || !a->inv_rho || !a->P || a->K0 == a->K1) {
@@ -3051,7 +3056,7 @@ dlra_status dlra_kstep(const dlra_kstep_args* args) {
   if (s != DLRA_OK) return (dlra_status)s;
   const bool two_d = args->ny == 1 && args->dy == 0.0;
   const long long n = (long long)args->nx * args->ny * args->nz;
-  const size_t bytes = kstep_scratch_bytes(n, args->r, two_d ? 2 : 3);
+  const size_t bytes = kstep_scratch_bytes(n, args->r, two_d ? 2 : 3, args->stage_kernel);
   void* scratch = nullptr;
   cudaError_t e = cudaMalloc(&scratch, bytes);
   if (e != cudaSuccess) {

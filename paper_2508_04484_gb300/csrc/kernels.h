@@ -187,7 +187,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn();
 
 // Work-space bytes of one stand-alone K-step (see dlra_kstep) and the step itself on
 // caller-provided device work space of at least that many bytes.
-size_t kstep_scratch_bytes(long long n, int r, int nact);
+size_t kstep_scratch_bytes(long long n, int r, int nact, int stage_kernel);
 int run_kstep(const void* args, void* scratch, size_t scratch_bytes, char* msg, int msg_len);
 
 }  // namespace dlra

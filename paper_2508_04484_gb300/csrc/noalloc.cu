@@ -43,7 +43,7 @@ extern "C" dlra_status dlra_kstep_noalloc(const dlra_kstep_args* args) {
     return DLRA_ERR_ARG;
   }
   const long long n = (long long)args->nx * args->ny * args->nz;
-  const size_t need = dlra::kstep_scratch_bytes(n, args->r, two_d ? 2 : 3);
+  const size_t need = dlra::kstep_scratch_bytes(n, args->r, two_d ? 2 : 3, args->stage_kernel);
   if (need == 0 || need > kNoAllocBytes) {
     std::snprintf(msg, sizeof msg,
                   "dlra_kstep_noalloc: n = %lld cells at r = %d need %zu bytes of work space; the static work space "

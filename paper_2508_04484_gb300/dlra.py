@@ -60,7 +60,7 @@ class dlra_kstep_args(C.Structure):
                 ("r", C.c_int32), ("e0", C.c_double), ("de", C.c_double), ("n_sub", C.c_int32),
                 ("bk_p", C.c_double), ("bk_alpha", C.c_double),
                 ("K0", C.c_void_p), ("K1", C.c_void_p), ("inv_rho", C.c_void_p), ("P", C.c_void_p),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("stage_kernel", C.c_int32)]
 
 
 class dlra_stencil_gram_args(C.Structure):
@@ -425,10 +425,11 @@ def dlra_kernel_stats(ctx):
 
 
 def kstep_args(grid: dict, r: int, e0: float, de: float, n_sub: int, K0, K1, inv_rho, P, stream=None,
-               bk_p=1.77, bk_alpha=0.0022):
+               bk_p=1.77, bk_alpha=0.0022, stage_kernel=0):
     """Argument block of dlra_kstep for torch CUDA float32 tensors K0, K1 (n x r
     column-major, i.e. shape (r, n)), inv_rho (n) and P (nk, r, r) with P_k
-    column-major (pass the transposes of the row-major r x r matrices)."""
+    column-major (pass the transposes of the row-major r x r matrices); stage_kernel as
+    Solver.set_stage_kernel."""
     a = dlra_kstep_args()
     a.nx, a.ny, a.nz = int(grid["nx"]), int(grid["ny"]), int(grid["nz"])
     a.dx, a.dy, a.dz = float(grid["dx"]), float(grid["dy"]), float(grid["dz"])
@@ -436,6 +437,7 @@ def kstep_args(grid: dict, r: int, e0: float, de: float, n_sub: int, K0, K1, inv
     a.bk_p, a.bk_alpha = float(bk_p), float(bk_alpha)
     a.K0, a.K1, a.inv_rho, a.P = K0.data_ptr(), K1.data_ptr(), inv_rho.data_ptr(), P.data_ptr()
     a.cuda_stream = stream
+    a.stage_kernel = int(stage_kernel)
     return a
 
 
