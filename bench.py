@@ -62,10 +62,12 @@ def _args():
                    help="skip the batched-against-plain comparison on the 64^3 eight-beam phantom")
     p.add_argument("--no-adjoint", action="store_true", help="skip timing the reverse sweep (dlra_backward)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
-    p.add_argument("--stage-kernel", type=int, choices=list(range(11)), default=None,
+    p.add_argument("--stage-kernel", type=int, choices=list(range(14)), default=None,
                    help="profiling: streaming-stage kernel (0 per-cell FMA, 1 tensor cores, 2 brick, 3 cell pairs, "
                         "4 / 5 TMA-staged tensor cores, 128 / 256-cell bricks, 6 persistent, 7 A in TMEM, "
-                        "8 2-CTA clusters, 9 three tiles along z, 10 eight-column chunks), set after the autotuner")
+                        "8 2-CTA clusters, 9 three tiles along z, 10 eight-column chunks, 11 eight formation warps, 12 five boxes and an FP32 B image, "
+                        "13 five boxes and the split B image), "
+                        "set after the autotuner")
     p.add_argument("--stencil-gram-kernel", type=int, choices=[0, 1, 2], default=None,
                    help="profiling: stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores with a TMA window), "
                         "set after the autotuner")
@@ -109,12 +111,19 @@ STAGE_KERNELS = {
         "}  // namespace dlra", "kstage_tmat.cuh"),
     10: ("kstage_tmaa8_kernel", "template <int RM>\n__global__ void __launch_bounds__(192) kstage_tmaa8_kernel(",
          "}  // namespace dlra", "kstage_tma8.cuh"),
+    11: ("kstage_tmaw_kernel", "template <int RM>\n__global__ void __launch_bounds__(320, 2) kstage_tmaw_kernel(",
+         "}  // namespace dlra", "kstage_tmaw.cuh"),
+    12: ("kstage_tmaf_kernel", "template <int RM, bool SPLIT>\n__global__ void __launch_bounds__(320, 2) kstage_tmaf_kernel(",
+         "}  // namespace dlra", "kstage_tmaf.cuh"),
+    13: ("kstage_tmaf_kernel", "template <int RM, bool SPLIT>\n__global__ void __launch_bounds__(320, 2) kstage_tmaf_kernel(",
+         "}  // namespace dlra", "kstage_tmaf.cuh"),
 }
 STAGE_NAMES = {"per-cell FMA": 0, "tensor cores": 1, "brick FMA": 2, "cell pairs": 3, "TMA tensor cores 128": 4,
                "TMA tensor cores 256": 5, "TMA tensor cores persistent": 6, "TMA tensor cores A in TMEM": 7,
                "TMA tensor cores cluster": 8,
                "TMA tensor cores 3 tiles": 9,
-               "TMA tensor cores 8 columns": 10}
+               "TMA tensor cores 8 columns": 10, "TMA tensor cores 8 formation warps": 11,
+               "TMA tensor cores faces": 12, "TMA tensor cores faces split B": 13}
 GRAM_NAMES = {"FMA": 0, "tensor cores": 1, "tensor cores TMA window": 2}
 APPLY_NAMES = {"FMA": 0, "tensor cores": 1}
 
@@ -625,7 +634,7 @@ def main():
               "durations": "profiled solve after the timed region (graph replay)" if use_graphs else "timed region",
               "traffic_gbs": traffic_gbs, "traffic_hbm_frac": traffic_gbs / hbm_peak if traffic_gbs else None,
               "counts": "per cell and launch (5r + 1) words and 2 nk r^2 + 6 nk r flops at the step's rank"}
-    if variant in (1, 4, 5, 6, 7, 8, 9, 10):
+    if variant in (1, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13):
         # the r x r mix on the tensor cores (kind::tf32, three products per FP32-accurate product):
         # the dense TF32 peak from the measured sustained bf16 GEMM rate x the nominal TF32/bf16 ratio
         bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))

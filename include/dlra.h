@@ -230,16 +230,17 @@ dlra_status dlra_set_adjoint_store(dlra_ctx* ctx, int32_t keep);
  * staged stencil inputs; the grid of the Gram reductions (608 / 1216 / 2432 / 4864 target
  * blocks) and of the stencil Grams (0.5 / 1 / 2 waves of the FMA kernel, and the tensor-core
  * kernel) and of the truncation apply (FMA or tensor cores). Needs materials and a beam;
- * synchronises; drops captured graphs. report (optional, 28 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
- * stencil-Gram grids, the chosen stage variant (0 .. 10 as dlra_set_stage_kernel), Gram block
+ * synchronises; drops captured graphs. report (optional, 31 doubles): ms of the per-cell and tensor-core stages, of the four Gram grids, of the three
+ * stencil-Gram grids, the chosen stage variant (0 .. 13 as dlra_set_stage_kernel), Gram block
  * target, stencil-Gram waves x 2, ms of the brick stage, ms of the tensor-core stencil Gram,
  * the chosen stencil-Gram kernel (0 FMA, 1 tensor cores), ms of the cell-pair stage, ms of
  * the TMA-staged tensor-core stages with 128- and 256-cell bricks, of its persistent form and
  * of its form with A in tensor memory, ms of the truncation apply with FMA and on the tensor
  * cores, the chosen apply kernel (0 FMA, 1 tensor cores), ms of the cluster form of the stage,
  * ms of the windowed stencil Gram, ms of the three-tile form of the stage, ms of the Gram
- * reduction on the tensor cores, ms of the eight-column form of the stage (-1 where not
- * applicable). */
+ * reduction on the tensor cores, ms of the eight-column form of the stage, ms of its form with
+ * eight formation warps, ms of its form with five boxes and an FP32 B image, ms of that form
+ * with the split B image (-1 where not applicable). */
 dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
 
 /* Streaming-stage kernel: 0 one thread per cell loading its 13 stencil neighbours (default),
@@ -258,8 +259,13 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report);
  * multicast bulk copy the chunk's B image into both CTAs (variant 7 where the cluster launch is
  * refused), 9 variant 7 on bricks of three 128-cell tiles stacked along z (8 x 4 x 12 cells, one
  * block per SM) sharing one halo box and one B image per chunk, 10 variant 7 on chunks of eight
- * input columns (half the chunks per brick). Same results up to rounding;
- * dlra_autotune picks among them. */
+ * input columns (half the chunks per brick), 11 variant 7 with eight formation warps, two per
+ * TMEM lane quarter, each forming the stencil values of two of the chunk's four columns, 12
+ * variant 11 staging each chunk as five TMA boxes (the brick with its x halo and its four y and z
+ * faces: half the values of the halo box, the stencil being a cross) and its B operand as one
+ * FP32 image that the formation warps split into TF32 parts in shared memory, 13 variant 12
+ * with the B image of TF32 high and low parts copied as it is (no split in shared memory). Same
+ * results up to rounding; dlra_autotune picks among them. */
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant);
 
 /* Kernel of the cell-side tall-skinny Grams (the augmentation's projections X^T K and the
@@ -338,7 +344,7 @@ typedef struct {
   const float* inv_rho;
   const float* P;
   void* cuda_stream;
-  int32_t stage_kernel; /* streaming-stage kernel, 0 .. 10 as dlra_set_stage_kernel (0: per-cell FMA) */
+  int32_t stage_kernel; /* streaming-stage kernel, 0 .. 13 as dlra_set_stage_kernel (0: per-cell FMA) */
 } dlra_kstep_args;
 
 /* The K-step of the streaming update (Sec. 2.2, Eq. KLS first line, with F_S of

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libdlra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "small.cu", "raytrace.cu", "adjoint.cu", "gram_tc.cu", "gram_win.cu", "gram_tt.cu", "noalloc.cu",
            "straggling.cu", "tables.cpp", "straggling_tables.cpp"]
-HEADERS = ["device.cuh", "kernels.h", "tables.h", "tcgen05.cuh", "kstage_tc.cuh", "kstage_tma.cuh", "kstage_tmac.cuh", "kstage_tmat.cuh", "kstage_tma8.cuh",
+HEADERS = ["device.cuh", "kernels.h", "tables.h", "tcgen05.cuh", "kstage_tc.cuh", "kstage_tma.cuh", "kstage_tmac.cuh", "kstage_tmat.cuh", "kstage_tma8.cuh", "kstage_tmaw.cuh", "kstage_tmaf.cuh",
            "apply_tc.cuh", "straggling_march.cuh"]
 
 

@@ -40,6 +40,8 @@
 #include "kstage_tmac.cuh"
 #include "kstage_tmat.cuh"
 #include "kstage_tma8.cuh"
+#include "kstage_tmaw.cuh"
+#include "kstage_tmaf.cuh"
 #include "apply_tc.cuh"
 #include "tables.h"
 
@@ -220,7 +222,10 @@ struct Tuning {
                               // 3 cell pairs, 4 / 5 TMA-staged tcgen05 with 128 / 256-cell bricks,
                               // 6 its persistent form, 7 with the A operand in tensor memory, 8 that on
                               // 2-CTA clusters with multicast halo and B copies, 9 that on bricks of three
-                              // 128-cell tiles along z, 10 variant 7 on chunks of eight columns
+                              // 128-cell tiles along z, 10 variant 7 on chunks of eight columns,
+                              // 11 variant 7 with eight formation warps (two column groups), 12 variant 11
+                              // staging the brick and its faces (five boxes) and an FP32 B image,
+                              // 13 variant 12 with the B image of TF32 high and low parts
   int gs_variant = 0;         // stencil Gram: 0 FMA, 1 tcgen05 (FP32 path), 2 tcgen05 with a TMA window (A == B, 3-D)
   int gs_tc_waves_x2 = 2;     // grid of the tensor-core stencil Gram, as gs_waves_x2
   int gram_variant = 0;       // tall-skinny Grams: 0 FMA, 1 tcgen05 (FP32 path, tall, at least 8 columns),
@@ -341,13 +346,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return tma_encode_fn();
 // as a 4-D tensor for TMA, box 16 x box_y x box_z x box_c (x, y, z, column). Needs nx and ld multiples
 // of 4 and a 16-byte aligned base (the tensor map's stride and address rules).
 bool stage_tensor_map(CUtensorMap* m, const float* vin, const Geo& g, long long ld, int rcap, int box_y,
-                      int box_z = 8, int box_c = 4) {
+                      int box_z = 8, int box_c = 4, int box_x = 16) {
   if (g.nx % 4 != 0 || ld % 4 != 0 || ((uintptr_t)vin & 15u) != 0 || g.nact != 3) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)rcap};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nxy * 4, (cuuint64_t)ld * 4};
-  const cuuint32_t box[4] = {16, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)box_c};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)box_c};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(vin), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -439,6 +444,51 @@ bool kstage_tmaa8_launch(cudaStream_t st, const float* vin, const float* y, floa
   return true;
 }
 
+// the A-in-TMEM stage with eight formation warps (128-cell bricks)
+template <int RM>
+bool kstage_tmaw_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                        int* err, void* bimg) {
+  using C = KsTmaW<RM>;
+  using B1 = KsTma<RM, 1>;
+  if (!bimg) return false;
+  CUtensorMap m;
+  if (!stage_tensor_map(&m, vin, g, n, RM, B1::BY)) return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  kstage_tma_bimg_kernel<RM, 1><<<nblk((long long)B1::NCH * B1::NP * B1::KC, 256), 256, 0, st>>>(Pst, rdim, img);
+  cudaFuncSetAttribute(kstage_tmaw_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  kstage_tmaw_kernel<RM><<<kstage_tma_grid<RM, 1>(g), C::THREADS, C::SMEM, st>>>(m, y, yout, vout, n, inv_rho, g, img,
+                                                                                rdim, beta, last, err);
+  return true;
+}
+
+// the eight-formation-warp stage on five boxes per chunk (128-cell bricks) with its B operand as
+// one FP32 image split in shared memory (SPLIT) or as the image of TF32 high and low parts
+template <int RM, bool SPLIT>
+bool kstage_tmaf_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
+                        const float* inv_rho, const Geo& g, const float* Pst, const int* rdim, float beta, int last,
+                        int* err, void* bimg) {
+  using C = KsTmaF<RM, SPLIT>;
+  using B1 = KsTma<RM, 1>;
+  if (!bimg) return false;
+  CUtensorMap mx, my, mz;
+  if (!stage_tensor_map(&mx, vin, g, n, RM, C::TY, C::TZ, C::CC, C::XW) ||
+      !stage_tensor_map(&my, vin, g, n, RM, 2, C::TZ, C::CC, C::TX) ||
+      !stage_tensor_map(&mz, vin, g, n, RM, C::TY, 2, C::CC, C::TX))
+    return false;
+  float* img = reinterpret_cast<float*>(bimg);
+  if (SPLIT)
+    kstage_tmaf_bimg_kernel<RM><<<nblk((long long)C::NCH * C::BSZ, 256), 256, 0, st>>>(Pst, rdim, img);
+  else
+    kstage_tma_bimg_kernel<RM, 1><<<nblk((long long)B1::NCH * B1::NP * B1::KC, 256), 256, 0, st>>>(Pst, rdim, img);
+  cudaFuncSetAttribute(kstage_tmaf_kernel<RM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  const unsigned grid = (unsigned)(((g.nx + C::TX - 1) / C::TX) * ((g.ny + C::TY - 1) / C::TY) *
+                                   ((g.nz + C::TZ - 1) / C::TZ));
+  kstage_tmaf_kernel<RM, SPLIT><<<grid, C::THREADS, C::SMEM, st>>>(mx, my, mz, y, yout, vout, n, inv_rho, g, img, rdim,
+                                                                   beta, last, err);
+  return true;
+}
+
 // the A-in-TMEM stage on bricks of T tiles stacked along z (one block per SM)
 template <int RM, int T>
 bool kstage_tmat_launch(cudaStream_t st, const float* vin, const float* y, float* yout, float* vout, long long n,
@@ -501,6 +551,19 @@ void kstage_launch(cudaStream_t st, const T* vin, const T* y, T* yout, T* vout, 
                    const Geo& g, const T* Pst, const int* rdim, T beta, int last, int* err, int variant,
                    void* bimg) {
   if constexpr (sizeof(T) == 4 && NACT == 3 && RM >= 32) {
+    if (variant == 12) {
+      if (kstage_tmaf_launch<RM, true>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
+      variant = 7;
+    }
+    if (variant == 13) {
+      if (kstage_tmaf_launch<RM, false>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg))
+        return;
+      variant = 7;
+    }
+    if (variant == 11) {
+      if (kstage_tmaw_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
+      variant = 7;
+    }
     if (variant == 10) {
       if (kstage_tmaa8_launch<RM>(st, vin, y, yout, vout, n, inv_rho, g, Pst, rdim, beta, last, err, bimg)) return;
       variant = 7;
@@ -2311,12 +2374,12 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   };
   Tuning t = ctx->tun;
   TuneScope scope(&t);
-  double rep[28] = {0};
+  double rep[31] = {0};
   // streaming stage: per-cell FMA, tensor cores (FP32 path), brick-staged FMA, cell pairs (FP32
   // path, nx even), TMA-staged tensor cores with 128- and 256-cell bricks (FP32 path, 3-D,
   // nx % 4 == 0, rank capacity >= 32)
-  double stage_ms[11];
-  for (int v = 0; v < 11; ++v) {
+  double stage_ms[14];
+  for (int v = 0; v < 14; ++v) {
     if ((v == 1 || v == 3 || v >= 4) && sizeof(T) != 4) {
       stage_ms[v] = -1.0;
       continue;
@@ -2402,7 +2465,7 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   cudaFree(flush);
   Tuning best = ctx->tun;
   int sv = 0;
-  for (int v = 1; v < 11; ++v)
+  for (int v = 1; v < 14; ++v)
     if (stage_ms[v] > 0.0 && stage_ms[v] < stage_ms[sv]) sv = v;
   best.kstage_variant = sv;
   int bi = 0;
@@ -2430,6 +2493,9 @@ dlra_status autotune_t(dlra_ctx* ctx, double* report) {
   rep[23] = stage_ms[8];
   rep[25] = stage_ms[9];
   rep[27] = stage_ms[10];
+  rep[28] = stage_ms[11];
+  rep[29] = stage_ms[12];
+  rep[30] = stage_ms[13];
   best.apply_variant = (apply_ms[1] > 0.0 && apply_ms[1] < apply_ms[0]) ? 1 : 0;
   rep[20] = apply_ms[0];
   rep[21] = apply_ms[1];
@@ -2540,8 +2606,8 @@ int check_kstep_args(const dlra_kstep_args* a, char* msg, int msg_len) {
     return DLRA_ERR_ARG;
   }
   if (a->r < 1 || a->r > 64 || a->n_sub < 1 || !(a->de > 0) || !(a->e0 - a->de > 0) || a->stage_kernel < 0 ||
-      a->stage_kernel > 10) {
-    std::snprintf(msg, msg_len, "need 1 <= r <= 64, n_sub >= 1, e0 > de > 0, stage kernel 0 .. 10");
+      a->stage_kernel > 13) {
+    std::snprintf(msg, msg_len, "need 1 <= r <= 64, n_sub >= 1, e0 > de > 0, stage kernel 0 .. 13");
     return DLRA_ERR_ARG;
   }
   if (!a->K0 || !a->K1 || !a->inv_rho || !a->P || a->K0 == a->K1) {
@@ -2878,7 +2944,7 @@ dlra_status dlra_autotune(dlra_ctx* ctx, double* report) {
 dlra_status dlra_set_stage_kernel(dlra_ctx* ctx, int32_t variant) {
   if (!ctx) return DLRA_ERR_ARG;
   if (ctx->poisoned) return ctx->poisoned;
-  if (variant < 0 || variant > 10) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 10");
+  if (variant < 0 || variant > 13) return fail(ctx, DLRA_ERR_ARG, "stage kernel variant must be 0 .. 13");
   CK(cudaStreamSynchronize(ctx->st));
   drop_graphs(ctx);
   ctx->tun.kstage_variant = variant;

@@ -358,19 +358,23 @@ def dlra_backward(ctx, dL_de, n_beams: int, n_mat: int, n: int, dw_out=None):
 
 def dlra_autotune(ctx):
     """Pick the fastest launch variants on this context; returns the timing report as a dict."""
-    rep = np.zeros(28)
+    rep = np.zeros(31)
     _check(ctx, load().dlra_autotune(ctx, _dptr(rep)))
     return dict(stage_fma_ms=rep[0], stage_tensor_core_ms=rep[1], stage_brick_ms=rep[12],
                 gram_ms=dict(zip((608, 1216, 2432, 4864), rep[2:6])),
                 stencil_gram_ms=dict(zip((0.5, 1.0, 2.0), rep[6:9])), stencil_gram_tc_ms=rep[13],
                 stage_pair_ms=rep[15], stage_tma128_ms=rep[16], stage_tma256_ms=rep[17],
                 stage_tma_persistent_ms=rep[18], stage_tma_tmem_a_ms=rep[19], stage_tma_cluster_ms=rep[23], stage_tma_tiles3_ms=rep[25], stage_tma_chunk8_ms=rep[27],
+                stage_tma_form8_ms=rep[28], stage_tma_faces_ms=rep[29],
+                stage_tma_faces_split_b_ms=rep[30],
                 apply_fma_ms=rep[20], apply_tensor_core_ms=rep[21],
                 apply_kernel=("FMA", "tensor cores")[int(rep[22])],
                 stage_variant=("per-cell FMA", "tensor cores", "brick FMA", "cell pairs", "TMA tensor cores 128",
                                "TMA tensor cores 256", "TMA tensor cores persistent",
                                "TMA tensor cores A in TMEM", "TMA tensor cores cluster",
-                               "TMA tensor cores 3 tiles", "TMA tensor cores 8 columns")[int(rep[9])],
+                               "TMA tensor cores 3 tiles", "TMA tensor cores 8 columns",
+                               "TMA tensor cores 8 formation warps", "TMA tensor cores faces",
+                               "TMA tensor cores faces split B")[int(rep[9])],
                 gram_blocks=int(rep[10]), stencil_gram_waves=rep[11] / 2.0,
                 stencil_gram_window_ms=rep[24], gram_tensor_core_ms=rep[26],
                 gram_kernel="tensor cores" if 0.0 < rep[26] < min(rep[2:6]) else "FMA",

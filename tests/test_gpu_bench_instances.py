@@ -128,7 +128,7 @@ def test_workload_kernel_instances_match_oracle(kind, precision):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
 @pytest.mark.parametrize("case", ["ragged", "phantom_128cube"])
 def test_tma_tensor_core_stage_matches_oracle(case, variant):
     # the TMA-staged tensor-core streaming stage (128- and 256-cell bricks) against the per-cell
