@@ -2,8 +2,9 @@
 phantom of seed 3), in the launch configurations the bench times, on sampled outputs that the
 oracle computes one by one.
 
-* The streaming K-step with the tensor-core stage the autotuner keeps (A operand in TMEM, kernel
-  7) at rank 60 (capacity 64), one RK4 sub-step (an energy step of 0.03 MeV): every output cell
+* The streaming K-step with the tensor-core stage the autotuner keeps (kernel 13: five TMA boxes
+  per chunk, eight formation warps, A operand in TMEM) and the one it kept before (kernel 7) at
+  rank 60 (capacity 64), one RK4 sub-step (an energy step of 0.03 MeV): every output cell
   depends on the input within eight cells (four stages of a two-cell stencil), so the oracle's
   K-step (Sec. 2.2 Eq. KLS, Sec. 3.3.2-3.3.3) on the 17^3 box around a sampled cell, with the
   same materials, gives that cell's K1 row exactly; cells on faces, edges and corners of the
@@ -102,7 +103,8 @@ def test_subbox_kstep_equals_full_grid():
 
 
 @pytest.mark.gpu
-def test_kstep_tensor_core_stage_full_size_sampled(built):
+@pytest.mark.parametrize("stage_kernel", [7, 13])
+def test_kstep_tensor_core_stage_full_size_sampled(built, stage_kernel):
     import torch
     from paper_2508_04484_gb300 import dlra as D
     cfg = _kstep_config(DIMS)
@@ -122,7 +124,7 @@ def test_kstep_tensor_core_stage_full_size_sampled(built):
     K1 = torch.zeros_like(K0)
     inv = torch.tensor(1.0 / rho_s, dtype=torch.float32, device=dev)
     P = torch.tensor(np.ascontiguousarray(np.transpose(np.array(Pk), (0, 2, 1))), dtype=torch.float32, device=dev)
-    a = D.kstep_args(cfg, r, prob.E[0], prob.h, 1, K0, K1, inv, P, stage_kernel=7)
+    a = D.kstep_args(cfg, r, prob.E[0], prob.h, 1, K0, K1, inv, P, stage_kernel=stage_kernel)
     D.dlra_kstep(a)
     torch.cuda.synchronize()
     K1h = K1.cpu().numpy()
@@ -133,7 +135,8 @@ def test_kstep_tensor_core_stage_full_size_sampled(built):
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         worst = max(worst, err)
         assert err < 1e-5, (c, err)
-    print(f"K-step at 128^3, rank 60, tensor-core stage: worst sampled-row error {worst:.2e} over {len(CELLS)} cells")
+    print(f"K-step at 128^3, rank 60, stage kernel {stage_kernel}: worst sampled-row error {worst:.2e} over "
+          f"{len(CELLS)} cells")
 
 
 @pytest.mark.gpu
