@@ -351,9 +351,9 @@ typedef struct {
  * Sec. 3.3.2 and RK4 time updates, Sec. 3.3.3): integrates
  * K' = S_w(E(t))^-1 sum_k D_k(rho_s^-1 K) P_k from K(t_k) = K0 over one energy step
  * with n_sub RK4 sub-steps, K1 = K(t_k + de), with the streaming-stage kernel
- * stage_kernel (the tensor-core kernels 4 .. 10 on 3-D grids with nx and n multiples of 4
+ * stage_kernel (the tensor-core kernels 4 .. 13 on 3-D grids with nx and n multiples of 4
  * and rank capacity >= 32, the per-cell FMA kernel otherwise). Allocates its work space
- * (3 n x r, the packed P and, for kernels 4 .. 10, the B images) with cudaMalloc and frees
+ * (3 n x r, the packed P and, for kernels 4 .. 13, the B images) with cudaMalloc and frees
  * it before returning; synchronises cuda_stream. */
 dlra_status dlra_kstep(const dlra_kstep_args* args);
 
@@ -364,7 +364,7 @@ dlra_status dlra_kstep(const dlra_kstep_args* args);
  * DLRA_ERR_ARG and a message naming both sizes. The work space is 3 n rcap +
  * 2 nact rcap^2 FP32 words (nact = 2 on an x-z slab, 3 in 3-D; rcap = r rounded
  * up to 4, 8, ..., 24, 32, 40, 48 or 64) plus up to 256 bytes of alignment per
- * buffer and one rank word, and with stage_kernel 4 .. 10 on a 3-D grid the B images of
+ * buffer and one rank word, and with stage_kernel 4 .. 13 on a 3-D grid the B images of
  * the tensor-core stages (2 x 6 rcap x round16(rcap) FP32 words). The first call on each device looks up the array's
  * device address with that device current and keeps it for the process; make
  * that first call before any stream capture. A cudaDeviceReset (or any other

@@ -64,6 +64,50 @@ __global__ void __launch_bounds__(256) kstage_tmaf_bimg_kernel(const float* __re
   img[(size_t)ch * BSZ + tc::kmajor(n, K, NP)] = (n < RM && c < r) ? Pst[((long long)c * NK + k) * RM + n] : 0.f;
 }
 
+// Float offsets (from the stage base) of a formation thread's cell (lx, ly, lz) and its 12
+// stencil neighbours in the five boxes of configuration C, for its warp group's first column
+// (column 2 grp of the chunk): 0 the cell, then per axis x, y, z the minus side (-1, -2) and the
+// plus side (+1, +2). The group's second column adds strd[j], the column stride of the box the
+// neighbour lies in (XCOL in the x box, FCOL in a face box). Host-callable so that the layout
+// can be checked on the CPU.
+template <class C>
+__host__ __device__ __forceinline__ void tmaf_offsets(int lx, int ly, int lz, int grp, int* off, int* strd) {
+  constexpr int TX = C::TX, TY = C::TY, TZ = C::TZ, XW = C::XW, XCOL = C::XCOL, FCOL = C::FCOL;
+  constexpr int OX = (int)(C::OFF_X / 4), OYL = (int)(C::OFF_YL / 4), OYH = (int)(C::OFF_YH / 4);
+  constexpr int OZL = (int)(C::OFF_ZL / 4), OZH = (int)(C::OFF_ZH / 4);
+  const int ca = 2 * grp;
+  auto xoff = [&](int zz, int yy, int xx) { return OX + ca * XCOL + (zz * TY + yy) * XW + xx + 4; };
+  off[0] = xoff(lz, ly, lx);
+  strd[0] = XCOL;
+  off[1] = off[0] - 1; off[2] = off[0] - 2; off[3] = off[0] + 1; off[4] = off[0] + 2;
+  strd[1] = strd[2] = strd[3] = strd[4] = XCOL;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int d = e < 2 ? -(e + 1) : e - 1;                        // -1, -2, +1, +2
+    const int yy = ly + d, zz = lz + d;
+    if (yy < 0) {
+      off[5 + e] = OYL + ca * FCOL + (lz * 2 + yy + 2) * TX + lx;
+      strd[5 + e] = FCOL;
+    } else if (yy >= TY) {
+      off[5 + e] = OYH + ca * FCOL + (lz * 2 + yy - TY) * TX + lx;
+      strd[5 + e] = FCOL;
+    } else {
+      off[5 + e] = xoff(lz, yy, lx);
+      strd[5 + e] = XCOL;
+    }
+    if (zz < 0) {
+      off[9 + e] = OZL + ca * FCOL + ((zz + 2) * TY + ly) * TX + lx;
+      strd[9 + e] = FCOL;
+    } else if (zz >= TZ) {
+      off[9 + e] = OZH + ca * FCOL + ((zz - TZ) * TY + ly) * TX + lx;
+      strd[9 + e] = FCOL;
+    } else {
+      off[9 + e] = xoff(zz, ly, lx);
+      strd[9 + e] = XCOL;
+    }
+  }
+}
+
 // mode: as kstage_kernel (0 vout = rho^-1 (y + beta acc); 1 also yout = y + beta acc, vout =
 // rho^-1 yout; 2 transposed operator: vout = beta rho^-1 acc, yout = y + vout). Tensor maps of
 // the stage input: mx with box (XW, 4, 4, CC), my (8, 2, 4, CC), mz (8, 4, 2, CC).
@@ -167,43 +211,8 @@ __global__ void __launch_bounds__(320, 2) kstage_tmaf_kernel(
     float inv2[3];
 #pragma unroll
     for (int da = 0; da < 3; ++da) inv2[da] = (float)g.inv2d[da];
-    // float offsets from the stage base of the cell and its 12 neighbours for the group's first
-    // column; the second column adds the box's column stride (XCOL in the x box, FCOL in a face)
-    constexpr int OX = (int)(C::OFF_X / 4), OYL = (int)(C::OFF_YL / 4), OYH = (int)(C::OFF_YH / 4);
-    constexpr int OZL = (int)(C::OFF_ZL / 4), OZH = (int)(C::OFF_ZH / 4);
-    const int ca = 2 * grp;
-    auto xoff = [&](int zz, int yy, int xx) { return OX + ca * XCOL + (zz * TY + yy) * XW + xx + 4; };
     int off[13], strd[13];
-    off[0] = xoff(lz, ly, lx);
-    strd[0] = XCOL;
-    // axis 0 (x): minus side x - 1, x - 2, plus side x + 1, x + 2
-    off[1] = off[0] - 1; off[2] = off[0] - 2; off[3] = off[0] + 1; off[4] = off[0] + 2;
-    strd[1] = strd[2] = strd[3] = strd[4] = XCOL;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int d = e < 2 ? -(e + 1) : e - 1;                      // -1, -2, +1, +2
-      const int yy = ly + d, zz = lz + d;
-      if (yy < 0) {
-        off[5 + e] = OYL + ca * FCOL + (lz * 2 + yy + 2) * TX + lx;
-        strd[5 + e] = FCOL;
-      } else if (yy >= TY) {
-        off[5 + e] = OYH + ca * FCOL + (lz * 2 + yy - TY) * TX + lx;
-        strd[5 + e] = FCOL;
-      } else {
-        off[5 + e] = xoff(lz, yy, lx);
-        strd[5 + e] = XCOL;
-      }
-      if (zz < 0) {
-        off[9 + e] = OZL + ca * FCOL + ((zz + 2) * TY + ly) * TX + lx;
-        strd[9 + e] = FCOL;
-      } else if (zz >= TZ) {
-        off[9 + e] = OZH + ca * FCOL + ((zz - TZ) * TY + ly) * TX + lx;
-        strd[9 + e] = FCOL;
-      } else {
-        off[9 + e] = xoff(zz, ly, lx);
-        strd[9 + e] = XCOL;
-      }
-    }
+    tmaf_offsets<C>(lx, ly, lz, grp, off, strd);
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     const int ftid = warp * 32 + lane;                               // 0 .. 255
     for (int ch = 0; ch < nch; ++ch) {
