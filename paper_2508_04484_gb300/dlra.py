@@ -630,7 +630,10 @@ class Solver:
         4 / 5 TMA-staged tensor cores with 128- / 256-cell bricks (FP32, 3-D, nx % 4 == 0, rank capacity >= 32),
         6 the same as one persistent CTA per SM with overlapped epilogue, 7 128-cell bricks with the A operand
         in tensor memory, 8 variant 7 on 2-CTA clusters sharing multicast halo and B copies, 9 variant 7 on
-        bricks of three tiles along z sharing one halo box and B image, 10 variant 7 on chunks of eight columns."""
+        bricks of three tiles along z sharing one halo box and B image, 10 variant 7 on chunks of eight columns,
+        11 variant 7 with eight formation warps, 12 variant 11 staging each chunk as five TMA boxes (brick with
+        its x halo, four y/z faces) with an FP32 B image split in shared memory, 13 variant 12 with the B image
+        copied already split."""
         dlra_set_stage_kernel(self.ctx, variant)
 
     def set_stencil_gram_kernel(self, variant):

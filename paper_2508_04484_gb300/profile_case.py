@@ -6,7 +6,8 @@ between replays, so it is run on a case a few GB in size whose buffers still exc
   python -m paper_2508_04484_gb300.profile_case stage --variant 4
       one energy step of a 96^3 three-material phantom (1.5 mm, P_21, rank 60 state, the
       128^3 workload's voxels, physics and rank capacity) with a chosen streaming-stage
-      kernel (0 per-cell FMA, 3 cell pairs, 4 / 5 / 6 TMA-staged tensor cores);
+      kernel (0 per-cell FMA, 3 cell pairs, 4 .. 13 the tensor-core forms of
+      Solver.set_stage_kernel, 13 the five-box form the autotuner keeps);
   python -m paper_2508_04484_gb300.profile_case gram --variant 2
       the same step with a chosen stencil-Gram kernel (0 FMA, 1 tensor cores, 2 tensor cores
       with the sliding TMA window); the step launches it twice (r x r and 2r x 2r);
